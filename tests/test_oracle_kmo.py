@@ -1,0 +1,200 @@
+"""Pins of the FP64 oracle's Kmouflage solver (Sec. 3.2.4 and Sec. 4.2 of
+arXiv:2110.00566) against closed forms and manufactured solutions."""
+import numpy as np
+import pytest
+
+from paper_2110_00566_gb300 import inputs
+
+
+def _fields(n, m, A, two_terms=True):
+    """u = A[sin(k1 x) sin(k2 y) + sin(k2 y) sin(k3 z)] at cell centres with
+    its gradient and Hessian (k_a = 2 pi m_a / n)."""
+    x = inputs.cell_centres(n)
+    k = [2 * np.pi * mm / n for mm in m]
+    X = np.meshgrid(x, x, x, indexing="ij")
+    s = [np.sin(k[a] * X[a]) for a in range(3)]
+    c = [np.cos(k[a] * X[a]) for a in range(3)]
+    u = A * (s[0] * s[1] + s[1] * s[2])
+    g = [A * k[0] * c[0] * s[1],
+         A * k[1] * c[1] * (s[0] + s[2]),
+         A * k[2] * s[1] * c[2]]
+    H = np.zeros((3, 3) + u.shape)
+    H[0, 0] = -A * k[0] ** 2 * s[0] * s[1]
+    H[1, 1] = -A * k[1] ** 2 * s[1] * (s[0] + s[2])
+    H[2, 2] = -A * k[2] ** 2 * s[1] * s[2]
+    H[0, 1] = H[1, 0] = A * k[0] * k[1] * c[0] * c[1]
+    H[1, 2] = H[2, 1] = A * k[1] * k[2] * c[1] * c[2]
+    H[0, 2] = H[2, 0] = 0.0
+    return u, np.array(g), H
+
+
+def _divergence_form(g, H, n_kmo, K1, gamma):
+    """nabla . [(K1 + gamma |grad u|^(2(n-1))) grad u] (Eq. kmo_eom1 over c~)
+    expanded by hand: K1 Lap u + gamma [G^(2(n-1)) Lap u
+    + 2 (n-1) G^(2(n-2)) u_i u_ij u_j]."""
+    G2 = (g ** 2).sum(axis=0)
+    lap = H[0, 0] + H[1, 1] + H[2, 2]
+    uHu = sum(g[a] * H[a, b] * g[b] for a in range(3) for b in range(3))
+    return K1 * lap + gamma * (G2 ** (n_kmo - 1) * lap + 2 * (n_kmo - 1) * G2 ** (n_kmo - 2) * uHu)
+
+
+@pytest.mark.parametrize("n_kmo", [2, 3])
+def test_kmo_operator_second_order(orc, n_kmo):
+    """Eq. kmf_eqn_codeunit_final with the discrete T: for a smooth u,
+    N_K(u) = (s + Sigma_2/c~)/Sigma_1 must approach Lap u when s is the
+    divergence form of Eq. kmo_eom1, at O(h^2).  This fixes the cross-term
+    coefficient: 1/(8h^4) converges, the printed 1/(2h^4) would leave an
+    O(1) error (checked below on the same field)."""
+    gamma, bterm = 0.8, 0.3
+    K1 = 1.0 + gamma * bterm ** (n_kmo - 1)
+    errs = []
+    for n in (32, 64, 128):
+        u, g, H = _fields(n, (1, 2, 1), A=n / 6.0)
+        s = _divergence_form(g, H, n_kmo, K1, gamma)
+        lap = H[0, 0] + H[1, 1] + H[2, 2]
+        op = orc.kmo_op(n_kmo, gamma, bterm)
+        Nk, _ = orc.N_field(op, u, s, 1.0)
+        errs.append(np.sqrt(np.mean((Nk - lap) ** 2)) / np.sqrt(np.mean(lap ** 2)))
+    assert 3.7 < errs[0] / errs[1] < 4.3 and 3.85 < errs[1] / errs[2] < 4.15, errs
+    # the printed 1/(2h^4) cross coefficient, applied by hand at n = 64:
+    n = 64
+    u, g, H = _fields(n, (1, 2, 1), A=n / 6.0)
+    s = _divergence_form(g, H, n_kmo, K1, gamma)
+    lap = H[0, 0] + H[1, 1] + H[2, 2]
+    G2 = (g ** 2).sum(axis=0)
+    # the printed coefficient adds (1/2 - 1/8) sum_{a<b} C_ab D_a D_b / h^4
+    # to T; with C_ab -> 4h^2 u_ab and D_a -> 2h u_a that is
+    # 6 sum_{a<b} u_ab u_a u_b, an O(1) change of N_K
+    extra_T = 3.0 * sum(2 * g[a] * H[a, b] * g[b] for a in range(3) for b in range(a + 1, 3))
+    sigma1 = K1 + (2 * n_kmo + 1) * gamma / 3 * G2 ** (n_kmo - 1)
+    shifted = -2 * (n_kmo - 1) * gamma * G2 ** (n_kmo - 2) * extra_T / sigma1
+    assert np.sqrt(np.mean(shifted ** 2)) > 20 * errs[1] * np.sqrt(np.mean(lap ** 2))
+
+
+def test_kmo_poisson_limit(orc):
+    """K0 = 0 (gamma = 0): Eq. kmf_eqn_codeunit_final is the Poisson
+    equation c~ Lap phi = 3 beta A Omega_m a^-1 delta; the MG solution equals
+    the FFT solution of the discrete Poisson equation."""
+    n, a, om, L = 32, 1.0, 0.3, 64.0
+    delta = inputs.white_noise(n, 3)
+    u, _ = orc.kmo_solve(delta, a, om, L, 2, 0.0, 0.2, 1.0, 0.0, 1.0, orc.Opts(rtol=1e-13, max_cycles=40))
+    s0, _ = orc.kmo_source(delta, a, om, n, L, 0.2, 1.0)
+    ref = orc.fft_poisson(s0)
+    assert np.abs(u - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_kmo_sine_1d(orc):
+    """Sec. 4.2.2: phi = A sin(kx) with the density that Eq. kmo_eom1 gives
+    for it (phibar' = 0, A(phibar) = 1):
+    delta = -(a c~/(3 beta Omega_m)) k^2 A sin(kx) [1 + (2n-1) gamma
+    (kA cos kx)^(2(n-1))].  The printed version of this density is garbled;
+    this is the form both Eq. kmo_eom1 and Eq. kmf_eqn_codeunit_final give.
+    The discrete solution approaches A sin(kx) at O(h^2)."""
+    a, om, beta, K0, nk, lam = 1.0, 0.3, 0.1, 1.0, 2, 1.0
+    gamma = orc.gamma_kmo(nk, K0, a, lam)
+    errs = []
+    for n in (16, 32, 64):
+        L = float(n)                         # c~ = c/H0 per cell of 1 Mpc/h
+        ct = orc.c_tilde(n, L)
+        A, K = n / 8.0, 1                     # strongly nonlinear: gamma (kA)^2 ~ 0.6
+        k = 2 * np.pi * K / n
+        x = inputs.cell_centres(n)[:, None, None]
+        shape = np.sin(k * x) * (1 + (2 * nk - 1) * gamma * (k * A * np.cos(k * x)) ** (2 * (nk - 1)))
+        delta = np.broadcast_to(-(a * ct / (3 * beta * om)) * k * k * A * shape, (n, n, n)).copy()
+        u, _ = orc.kmo_solve(delta, a, om, L, nk, K0, beta, lam, 0.0, 1.0, orc.Opts(rtol=1e-12, max_cycles=60))
+        exact = np.broadcast_to(A * np.sin(k * x), (n, n, n))
+        errs.append(np.abs(u - exact).max() / A)
+    assert 3.6 < errs[0] / errs[1] < 4.4 and 3.8 < errs[1] / errs[2] < 4.2, errs
+    # the paper's parameters (n=2, K0=1, beta=0.1, A=0.1, K=4) on N = 64
+    n, A, K = 64, 0.1, 4
+    L = 64.0
+    ct = orc.c_tilde(n, L)
+    k = 2 * np.pi * K / n
+    x = inputs.cell_centres(n)[:, None, None]
+    shape = np.sin(k * x) * (1 + (2 * nk - 1) * gamma * (k * A * np.cos(k * x)) ** 2)
+    delta = np.broadcast_to(-(a * ct / (3 * beta * om)) * k * k * A * shape, (n, n, n)).copy()
+    u, _ = orc.kmo_solve(delta, a, om, L, nk, K0, beta, lam, 0.0, 1.0, orc.Opts(rtol=1e-10))
+    assert np.abs(u - A * np.sin(k * x)).max() < 0.02 * A
+
+
+@pytest.mark.parametrize("n_kmo", [2, 3])
+def test_kmo_manufactured_3d(orc, n_kmo):
+    """Manufactured 3D solution u* = A[sin(kx)sin(ky) + sin(ky)sin(kz)] with
+    the density from the divergence form of Eq. kmo_eom1: the discrete
+    solution converges to u* at O(h^2) (pins the 19-point T with the
+    1/(8h^4) cross coefficient)."""
+    gamma, bterm = 0.8, 0.0
+    errs = []
+    for n in (16, 32, 64):
+        u, g, H = _fields(n, (1, 1, 1), A=n / 8.0)
+        s = _divergence_form(g, H, n_kmo, 1.0, gamma)
+        s = s - s.mean()
+        op = orc.kmo_op(n_kmo, gamma, bterm)
+        sol, st = orc.mg_solve(op, s, float(np.sqrt(np.mean(s ** 2))), orc.Opts(rtol=1e-12, max_cycles=80))
+        errs.append(np.abs(sol - (u - u.mean())).max() / np.abs(u).max())
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.8 < errs[1] / errs[2] < 4.2, errs
+
+
+def _cardano(f, gamma):
+    """Sec. 4.2.3 printed root of gamma y^3 + y = f:
+    y = g^(1/3)/(6 gamma) - 2/g^(1/3), g = gamma^2[108 f + 20.78460969
+    sqrt(27 f^2 + 4/gamma)] (20.78460969 = 12 sqrt(3))."""
+    g = gamma ** 2 * (108 * f + 20.78460969 * np.sqrt(27 * f ** 2 + 4 / gamma))
+    return np.cbrt(g) / (6 * gamma) - 2 / np.cbrt(g)
+
+
+def test_kmo_sphere_cubic_root(orc):
+    """The printed spherical solution (Sec. 4.2.3) is the real root of the
+    cubic gamma y^3 + y = f that Eq. Kmo_eom_spherical1 gives for n = 2."""
+    for gamma in (1.0, 10.0, 100.0):
+        for f in (1e-3, 0.1, 1.0, 30.0):
+            y = _cardano(f, gamma)
+            assert gamma * y ** 3 + y == pytest.approx(f, rel=1e-7)
+
+
+def test_kmo_sphere_shape(orc):
+    """Sec. 4.2.3: delta = 5000 in a sphere of R = 0.1 N, n = 2, beta = 0.2,
+    K0 = 1, 10, 100 (gamma = K0 at a = lambda = 1).  The radial gradient of
+    the solution near the centre agrees with the cubic root to a few per
+    cent (periodic images and O(h^2) limit it)."""
+    n, a, om, beta, L = 64, 1.0, 0.3, 0.2, 64.0
+    R = 0.1 * n
+    delta = inputs.tophat_sphere(n, R, 5000.0)
+    dbar = delta.mean()
+    ct = orc.c_tilde(n, L)
+    c = n // 2
+    for K0 in (1.0, 10.0, 100.0):
+        gamma = orc.gamma_kmo(2, K0, a, 1.0)
+        u, _ = orc.kmo_solve(delta, a, om, L, 2, K0, beta, 1.0, 0.0, 1.0, orc.Opts(rtol=1e-10))
+        for m in (1, 2, 3, 4):
+            r = np.sqrt(m ** 2 + 0.5)
+            d_enc = (5000.0 * min(1.0, (R / r) ** 3)) - dbar    # mean delta - <delta> within r
+            f = beta * om / ct * d_enc * r
+            expect = _cardano(f, gamma) * m / r
+            got = u[c + m, c, c] - u[c + m - 1, c, c]
+            assert got == pytest.approx(expect, rel=0.06), (K0, m, got, expect)
+
+
+def test_kmo_uniform(orc):
+    """Sec. 4.2.1 for Kmouflage: delta = 0 relaxes to a constant."""
+    n = 16
+    u0 = inputs.uniform_guess(n, seed=1)
+    u, _ = orc.kmo_solve(np.zeros((n,) * 3), 1.0, 0.3, 16.0, 2, 1.0, 0.2, 1.0, 0.0, 1.0,
+                         orc.Opts(rtol=0.0, atol=1e-13, max_cycles=60), u0)
+    assert np.abs(u).max() < 1e-12
+
+
+@pytest.mark.parametrize("n_kmo,amp,gamma", [(2, 0.05, 50.0), (3, 0.3, 2e4)])
+def test_kmo_mg_matches_newton(orc, n_kmo, amp, gamma):
+    """FAS V-cycles reach the root of the discrete Kmouflage system found by
+    a dense Newton solve on an 8^3 mesh."""
+    from test_oracle_ndgp import _newton_solve
+    n = 8
+    s0 = inputs.white_noise(n, 77)
+    s0 = amp * (s0 - s0.mean())
+    op = orc.kmo_op(n_kmo, gamma, 0.01)
+    un = _newton_solve(orc, op, s0, n)
+    u, _ = orc.mg_solve(op, s0, float(np.sqrt(np.mean(s0 ** 2))), orc.Opts(rtol=1e-14, max_cycles=80))
+    assert np.linalg.norm(u - un) < 1e-10 * np.linalg.norm(un)
+    lin = orc.fft_poisson(s0 / (1 + gamma * 0.01 ** (n_kmo - 1)))
+    assert np.linalg.norm(u - lin) > 1e-3 * np.linalg.norm(lin)
