@@ -1,0 +1,300 @@
+/*
+ * mgglam.h -- C-ABI of libmgglam.so, the GB300 (sm_103a) implementation of
+ * the MG-GLAM derivative-coupling field solvers of Hernandez-Aguayo et al.,
+ * "Fast full N-body simulations of generic modified gravity: derivative
+ * coupling models" (arXiv:2110.00566).
+ *
+ * Conventions for every call below
+ * --------------------------------
+ *  - Code units of the paper's Sec. 3.1.1: a mesh of ng^3 cells of size
+ *    h = 1 on the finest level; positions x~ in [0, ng); potentials
+ *    Phi~ = (ng/(H0 L))^2 Phi; the nDGP field phi~ in the same unit; the
+ *    Kmouflage field phi~ = c~ phi (Eq. Kmo_unit), c~ = (c/H0) ng / L.
+ *  - Mesh arrays are C-ordered (i, j, k) with k fastest, ng^3 elements, cell
+ *    (i, j, k) centred at (i+1/2, j+1/2, k+1/2).  Particle arrays are np x 3.
+ *  - Pointers may be device pointers on the context's device or host
+ *    pointers (pageable or pinned); the library detects which with
+ *    cudaPointerGetAttributes and stages host data through its own device
+ *    workspace.  All arrays are owned by the caller; the library owns only
+ *    the workspace inside mg_ctx (level pyramids, staging and reduction
+ *    buffers, CUDA graphs), allocated on first use for a given mesh size
+ *    and precision and kept until mg_ctx_destroy.
+ *  - Calls are issued on the context's stream.  Calls that return a
+ *    statistics record synchronise that stream before returning; the
+ *    others return once the work is queued (device pointers) or done (host
+ *    pointers).  One context must not be used from two host threads at once.
+ *  - Return value: MG_OK (0), a warning (> 0: the result is valid), or an
+ *    error (< 0: the outputs are unspecified); mg_last_error_string() gives
+ *    the detail of the last error or warning.
+ */
+#ifndef MGGLAM_H
+#define MGGLAM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------- */
+#define MG_OK                   0
+#define MG_WARN_NOT_CONVERGED   1   /* max_cycles reached; phi still returned */
+#define MG_ERR_ARG             -1   /* null pointer, unsupported size, bad option */
+#define MG_ERR_CUDA            -2   /* a CUDA runtime or cuFFT call failed */
+#define MG_ERR_TIMEOUT         -3   /* a bounded device-side wait gave up */
+#define MG_ERR_NONFINITE       -4   /* NaN/Inf in an input or a residual norm */
+#define MG_ERR_OOM             -5   /* device workspace allocation failed */
+
+/* ---- context ---------------------------------------------------------- */
+typedef struct mg_ctx mg_ctx;
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to
+ * issue all work on, or NULL to let the context create its own.
+ * Errors: MG_ERR_ARG (out == NULL), MG_ERR_CUDA (bad device). */
+int mg_ctx_create(mg_ctx **out, int device, void *cuda_stream);
+
+/* Free the workspace and the context (a NULL argument is ignored). */
+void mg_ctx_destroy(mg_ctx *ctx);
+
+/* Detail of the last error or warning of this context (never NULL). */
+const char *mg_last_error_string(const mg_ctx *ctx);
+
+/* Device bytes currently held by the context's workspace. */
+long long mg_ctx_workspace_bytes(const mg_ctx *ctx);
+
+/* on != 0: bracket every finest-level smoother launch of the following
+ * solves with CUDA events (recorded inside the captured cycle graphs) and
+ * report their summed device time in mg_stats.fine_smooth_ms.  Returns
+ * MG_OK or MG_ERR_ARG (ctx == NULL). */
+int mg_ctx_set_profiling(mg_ctx *ctx, int on);
+
+/* Measured FP64 and FP32 fused multiply-add throughput of the context's
+ * device in TFLOP/s (an FMA counts 2), from eight independent FMA chains
+ * per thread on 16 CTAs per SM: the denominator for kernels bound by plain
+ * ALU arithmetic.  Either output may be NULL.  Blocks until done.  (The
+ * paper has no counterpart; this is measurement support.) */
+int mg_probe_alu_peaks(mg_ctx *ctx, double *fp64_tflops, double *fp32_tflops);
+
+/* ---- problem description (Sec. 3.1.1, 3.2.3, 3.2.4) ------------------- */
+typedef struct {
+    int ng;            /* cells per side: 2^k or 3 * 2^k, ng >= 8 (levels halve
+                          to a 4^3 or 6^3 coarsest mesh, Sec. 3.2.1)          */
+    double box_mpch;   /* box side L in Mpc/h                                  */
+    double a;          /* scale factor                                         */
+    double omega_m;    /* present-day matter density parameter                 */
+} mg_grid;
+
+/* nDGP: R_c = H0 r_c / c (Sec. 3.2.3); beta_DGP(a) of Eq. beta_dgp for the
+ * LCDM-matched background and alpha = 3 beta a^2 / R_c^2 are derived. */
+typedef struct {
+    double rc_h0;
+} mg_dgp_params;
+
+/* Kmouflage, K(X) = -1 + X + K0 X^n, A = exp(beta phi) (Sec. 2.2, 3.2.4):
+ * gamma = n K0 (1/(2 a^2 lambda^2))^(n-1) is derived; the background
+ * phibar'/H0 and A(phibar) are inputs (the background solver is not part
+ * of this library). */
+typedef struct {
+    int n;                        /* exponent, n >= 2                          */
+    double k0;                    /* K0 >= 0                                   */
+    double beta_kmo;              /* coupling beta_Kmo                         */
+    double lambda;                /* lambda of Lambda^4/M_Pl^2 = H0^2 lambda^2 */
+    double phibar_prime_over_h0;  /* phibar' / H0 (conformal-time derivative)  */
+    double A_bar;                 /* A(phibar)                                 */
+} mg_kmo_params;
+
+/* ---- solver options ---------------------------------------------------- */
+#define MG_CYCLE_V 0
+#define MG_CYCLE_F 1
+#define MG_CYCLE_W 2
+#define MG_PREC_FP64  0   /* every level in FP64                             */
+#define MG_PREC_MIXED 1   /* FP32 FAS cycles on the correction, FP64
+                             finest-level defect, norms and coarsest solve   */
+
+typedef struct {
+    int pre, post;        /* red-black sweeps before / after the coarse-grid
+                             correction on every level (paper: 2 and 2)       */
+    int max_cycles;       /* <= 64                                            */
+    int cycle;            /* MG_CYCLE_V / _F / _W (Sec. 3.2.1)                */
+    int precision;        /* MG_PREC_FP64 / MG_PREC_MIXED                     */
+    double rtol, atol;    /* stop when eps <= rtol * eps_ref + atol, eps =
+                             rms of the finest residual (Sec. 3.2.1)         */
+    int warm_start;       /* 1: phi holds the initial guess; 0: start at 0    */
+    int coarse_sweeps;    /* red-black sweeps on the coarsest level           */
+    int use_graph;        /* 1: replay each cycle from a captured CUDA graph  */
+    int inner_cycles;     /* MIXED: FP32 cycles per FP64 defect correction    */
+} mg_opts;
+
+/* pre = post = 2, max_cycles = 30, V, FP64, rtol = 1e-8, atol = 0,
+ * warm_start = 0, coarse_sweeps = 64, use_graph = 1, inner_cycles = 2. */
+void mg_opts_default(mg_opts *o);
+
+typedef struct {
+    int cycles;              /* cycles run (FP64: V/F/W cycles; MIXED: FP32
+                                inner cycles in total)                         */
+    int status;              /* the call's return code                          */
+    double eps_ref;          /* nDGP: rms(Omega_m a^-1 delta / beta);
+                                Kmouflage: rms(3 beta A Omega_m a^-1 delta/c~)  */
+    double eps[65];          /* eps[0] initial, then after each cycle (MIXED:
+                                after each defect correction)                   */
+    int n_eps;               /* entries of eps[] written                        */
+    double c_final;          /* <N(phi)>, the compatibility constant            */
+    double mean_shift;       /* mean removed from phi (gauge <phi> = 0)          */
+    long long sqrt_clamps;   /* nDGP cells whose sqrt argument was clamped at 0 */
+    double ms;               /* wall time of the solve on the stream (ms)       */
+    long long cell_updates;  /* smoother cell-updates summed over all levels    */
+    long long kernel_launches;      /* CUDA kernels launched by the solve       */
+    double fine_smooth_ms;          /* with profiling on: summed device time of
+                                       the finest-level smoother launches (ms)  */
+    long long fine_smooth_launches; /* ... and their number                     */
+} mg_stats;
+
+typedef struct {
+    mg_grid g;
+    mg_dgp_params p;
+    const double *delta;     /* ng^3 density contrast                            */
+    double *phi;             /* ng^3 output (and guess if warm_start)            */
+} mg_instance;
+
+/* ---- the hot path ------------------------------------------------------ */
+
+/*
+ * nDGP scalar field (Eq. dgp_eom_code in the form of Eq. DGP):
+ *   Lap phi = (3/4)[-alpha + sqrt(alpha^2 + 8 Sigma / 3)],
+ *   Sigma = traceless (d_i d_j phi)^2 + (alpha / beta) Omega_m a^-1 delta,
+ * discretised as the paper's L^h with the 19-point Sigma_ijk (Sec. 3.2.3)
+ * and solved by FAS multigrid (Sec. 3.2.1) with the colour-simultaneous
+ * red-black update of Eq. nonlinear_GS_DGP.  delta - <delta> is used; the
+ * periodic system is made compatible by L(u) = Lap u - N(u) + <N(u)>, and
+ * the result has <phi> = 0.
+ * count >= 1 independent instances (sizes may differ); count > 1 is the
+ * batched form: all instances advance together, one fused launch per
+ * multigrid step across the batch.  stats: `count` records (or NULL).
+ * Returns MG_OK, MG_WARN_NOT_CONVERGED, MG_ERR_ARG, MG_ERR_CUDA,
+ * MG_ERR_NONFINITE or MG_ERR_OOM.
+ */
+int mg_solve_dgp(mg_ctx *ctx, int count, const mg_instance *inst,
+                 const mg_opts *opts, mg_stats *stats);
+
+/*
+ * Kmouflage field (Eq. kmo_eom1 in the split form of Eq.
+ * kmf_eqn_codeunit_final, divided by c~):
+ *   Lap phi = [3 beta A Omega_m a^-1 delta / c~ - 2 (n-1) gamma (G^2)^(n-2) T]
+ *             / [1 + gamma (phibar'/H0)^(2(n-1)) + (2n+1) gamma/3 (G^2)^(n-1)],
+ * G the central-difference gradient, T the 19-point
+ * hat-nabla^i hat-nabla^j phi nabla_i phi nabla_j phi (cross terms with
+ * 1/(8h^4)).  Same multigrid, options and errors as mg_solve_dgp.
+ */
+int mg_solve_kmouflage(mg_ctx *ctx, const mg_grid *g, const mg_kmo_params *p,
+                       const mg_opts *opts, const double *delta, double *phi,
+                       mg_stats *stats);
+
+/*
+ * Cloud-in-cell density contrast (Sec. 3.1): each of the np particles
+ * (FP32 positions in [0, ng), np x 3) carries (ng^3/np) mean cell masses
+ * spread over the 8 cells around it; delta_out = rho/rho_bar - 1 (ng^3,
+ * FP64, mean removed).  The lower cell per axis is floor(x - 1/2) taken in
+ * FP32.  Deterministic: weights are summed as 32.32 fixed point in 64-bit
+ * integers.  Errors: MG_ERR_ARG (bad sizes, positions outside [0, ng) are
+ * wrapped, never rejected), MG_ERR_CUDA, MG_ERR_OOM.
+ */
+int pm_cic_deposit(mg_ctx *ctx, int ng, const float *pos, long long np,
+                   double *delta_out);
+
+/* Lower CIC cell per axis, floor(x - 1/2) mod ng, as used by
+ * pm_cic_deposit (np x 3 int32 output); for checking the indexing. */
+int pm_cic_index(mg_ctx *ctx, int ng, const float *pos, long long np,
+                 int *idx_out);
+
+/*
+ * Particle-mesh state for pm_step: positions x~ (FP32, np x 3, in [0, ng))
+ * at scale factor a, momenta p~ (FP32, np x 3) at a - da/2 (at a itself
+ * when first != 0).  model 0 = GR (Newtonian force only), 1 = nDGP
+ * (Phi = Phi_N + phi/2, Eq. poisson_nDGP).  phi_ws: ng^3 FP64 device or
+ * host buffer carrying the nDGP field between steps as a warm start (may be
+ * NULL; then each solve starts from zero).
+ */
+typedef struct {
+    float *pos, *mom;
+    long long np;
+    int ng;
+    double box_mpch, omega_m, a, da;
+    int model;
+    int first;
+    mg_dgp_params dgp;
+    double *phi_ws;
+} pm_state;
+
+/*
+ * One leapfrog step in a (code-unit equations of motion of Sec. 3.1.1 with
+ * the drift sign of Eq. force_Kmo1): CIC density, FFT Poisson solve of
+ * Lap Phi_N = (3/2) Omega_m a^-1 delta with the 7-point Green's function,
+ * the nDGP field (model 1), 3-point gradient of Phi at the 8 CIC cells
+ * interpolated to each particle, kick p += g da/(a E(a)) (da/2 if first),
+ * drift x += p da/(a_m^3 E(a_m)) with a_m = a + da/2, wrap into [0, ng).
+ * Updates pos, mom, a (+= da) and first (= 0).  stats: the nDGP solve.
+ */
+int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats);
+
+/*
+ * Adjoint of the nDGP solve: given the forward solution phi for delta and
+ * a cotangent g = dLoss/dphi, solves J^T lambda = g (J the Jacobian of the
+ * discrete operator of mg_solve_dgp, restricted to zero-mean fields) by a
+ * linear multigrid on J^T and returns dLoss/ddelta = (dN/ddelta)^T lambda
+ * (ng^3) and dLoss/dR_c (one FP64 scalar written to a HOST pointer).  Both
+ * outputs are exact gradients of the discrete solution map at the given
+ * tolerance.  dL_drc_out may be NULL.
+ */
+int mg_solve_adjoint(mg_ctx *ctx, const mg_grid *g, const mg_dgp_params *p,
+                     const mg_opts *opts, const double *phi, const double *delta,
+                     const double *dL_dphi, double *dL_ddelta_out,
+                     double *dL_drc_out, mg_stats *stats);
+
+/* ---- kernel-level entry points (one multigrid step each) ---------------
+ * For checking each kernel against a reference implementation.  Natural
+ * layout FP64 in and out on the context's device (or host); `precision`
+ * selects the FP64 (0) or FP32 (1) kernel (inputs are rounded to FP32 on
+ * the way in for 1).  The operator is given explicitly:                   */
+typedef struct {
+    int model;        /* 0 = nDGP, 1 = Kmouflage                             */
+    double alpha;     /* nDGP alpha                                          */
+    int nkmo;         /* Kmouflage n                                         */
+    double gamma;     /* Kmouflage gamma                                     */
+    double bterm;     /* Kmouflage (phibar'/H0)^2                            */
+} mg_op_params;
+
+/* One colour-simultaneous half-sweep of Eq. nonlinear_GS_DGP on an n^3
+ * level of spacing h with compatibility constant c: cells of `colour`
+ * ((i+j+k) mod 2) get (sum of face neighbours - h^2 (N - c + f)) / 6, the
+ * other colour is copied.  f may be NULL (zero). */
+int mg_op_smooth(mg_ctx *ctx, const mg_op_params *op, int precision, int n,
+                 double h, const double *u_in, const double *s, const double *f,
+                 double c, int colour, double *u_out);
+
+/* Fused residual and FAS restriction (Sec. 3.2.1): with c_new = <N(u)>,
+ * d = Lap u - N + c_new - f; writes R u and R d ((n/2)^3 each, 8-cell
+ * averages), c_new and eps = rms(d) (host scalars). */
+int mg_op_resid_restrict(mg_ctx *ctx, const mg_op_params *op, int precision,
+                         int n, double h, const double *u, const double *s,
+                         const double *f, double *Ru, double *Rd,
+                         double *c_out, double *eps_out);
+
+/* Coarse FAS source (Eq. general_pde_numerical_coarse): on an n^3 coarse
+ * level, f = L^H(Ru) - Rd with L^H including its own c = <N^H(Ru)>;
+ * writes f and c (host scalar). */
+int mg_op_coarse_source(mg_ctx *ctx, const mg_op_params *op, int precision,
+                        int n, double h, const double *Ru, const double *Rd,
+                        const double *s, double *f_out, double *c_out);
+
+/* Correction (Eq. solution_correction): u_fine += P(uc - urc) with the
+ * 27/9/3/1 over 64 prolongation; n = fine size. */
+int mg_op_prolong_add(mg_ctx *ctx, int precision, int n, double *u_fine,
+                      const double *uc, const double *urc);
+
+/* Coarsest-level solve: `sweeps` times { c = <N(u)>; red-black sweep },
+ * in FP64 in shared memory (n^3 <= 512). */
+int mg_op_coarsest(mg_ctx *ctx, const mg_op_params *op, int n, double h,
+                   double *u, const double *s, const double *f, int sweeps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGGLAM_H */

@@ -1,0 +1,316 @@
+"""Thin ctypes binding of libmgglam.so (include/mgglam.h).
+
+Argument marshalling only: every step of the solvers runs in the CUDA
+library.  Functions carry the C names and accept torch tensors (CUDA or
+CPU) or numpy arrays for the array arguments; CPU arrays are staged by the
+library itself.  The library is loaded on first use; if it is missing or
+cannot be loaded, an ImportError is raised -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmgglam.so")
+
+MG_OK = 0
+MG_WARN_NOT_CONVERGED = 1
+MG_ERR_ARG = -1
+MG_ERR_CUDA = -2
+MG_ERR_TIMEOUT = -3
+MG_ERR_NONFINITE = -4
+MG_ERR_OOM = -5
+MG_CYCLE_V, MG_CYCLE_F, MG_CYCLE_W = 0, 1, 2
+MG_PREC_FP64, MG_PREC_MIXED = 0, 1
+
+
+class mg_grid(C.Structure):
+    _fields_ = [("ng", C.c_int), ("box_mpch", C.c_double), ("a", C.c_double), ("omega_m", C.c_double)]
+
+
+class mg_dgp_params(C.Structure):
+    _fields_ = [("rc_h0", C.c_double)]
+
+
+class mg_kmo_params(C.Structure):
+    _fields_ = [("n", C.c_int), ("k0", C.c_double), ("beta_kmo", C.c_double), ("lambda_", C.c_double),
+                ("phibar_prime_over_h0", C.c_double), ("A_bar", C.c_double)]
+
+
+class mg_opts(C.Structure):
+    _fields_ = [("pre", C.c_int), ("post", C.c_int), ("max_cycles", C.c_int), ("cycle", C.c_int),
+                ("precision", C.c_int), ("rtol", C.c_double), ("atol", C.c_double),
+                ("warm_start", C.c_int), ("coarse_sweeps", C.c_int), ("use_graph", C.c_int),
+                ("inner_cycles", C.c_int)]
+
+
+class mg_stats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("status", C.c_int), ("eps_ref", C.c_double),
+                ("eps", C.c_double * 65), ("n_eps", C.c_int), ("c_final", C.c_double),
+                ("mean_shift", C.c_double), ("sqrt_clamps", C.c_longlong), ("ms", C.c_double),
+                ("cell_updates", C.c_longlong), ("kernel_launches", C.c_longlong),
+                ("fine_smooth_ms", C.c_double), ("fine_smooth_launches", C.c_longlong)]
+
+    def eps_list(self):
+        return list(self.eps[: self.n_eps])
+
+
+class mg_instance(C.Structure):
+    _fields_ = [("g", mg_grid), ("p", mg_dgp_params), ("delta", C.c_void_p), ("phi", C.c_void_p)]
+
+
+class pm_state(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("mom", C.c_void_p), ("np", C.c_longlong), ("ng", C.c_int),
+                ("box_mpch", C.c_double), ("omega_m", C.c_double), ("a", C.c_double), ("da", C.c_double),
+                ("model", C.c_int), ("first", C.c_int), ("dgp", mg_dgp_params), ("phi_ws", C.c_void_p)]
+
+
+class mg_op_params(C.Structure):
+    _fields_ = [("model", C.c_int), ("alpha", C.c_double), ("nkmo", C.c_int), ("gamma", C.c_double),
+                ("bterm", C.c_double)]
+
+
+_lib = None
+_VP = C.c_void_p
+_P = C.POINTER
+
+
+def _declare(L):
+    sig = {
+        "mg_ctx_create": (C.c_int, [_P(C.c_void_p), C.c_int, _VP]),
+        "mg_ctx_destroy": (None, [_VP]),
+        "mg_last_error_string": (C.c_char_p, [_VP]),
+        "mg_ctx_workspace_bytes": (C.c_longlong, [_VP]),
+        "mg_ctx_set_profiling": (C.c_int, [_VP, C.c_int]),
+        "mg_probe_alu_peaks": (C.c_int, [_VP, _P(C.c_double), _P(C.c_double)]),
+        "mg_opts_default": (None, [_P(mg_opts)]),
+        "mg_solve_dgp": (C.c_int, [_VP, C.c_int, _P(mg_instance), _P(mg_opts), _P(mg_stats)]),
+        "mg_solve_kmouflage": (C.c_int, [_VP, _P(mg_grid), _P(mg_kmo_params), _P(mg_opts), _VP, _VP,
+                                         _P(mg_stats)]),
+        "pm_cic_deposit": (C.c_int, [_VP, C.c_int, _VP, C.c_longlong, _VP]),
+        "pm_cic_index": (C.c_int, [_VP, C.c_int, _VP, C.c_longlong, _VP]),
+        "pm_step": (C.c_int, [_VP, _P(pm_state), _P(mg_opts), _P(mg_stats)]),
+        "mg_solve_adjoint": (C.c_int, [_VP, _P(mg_grid), _P(mg_dgp_params), _P(mg_opts), _VP, _VP, _VP, _VP,
+                                       _VP, _P(mg_stats)]),
+        "mg_op_smooth": (C.c_int, [_VP, _P(mg_op_params), C.c_int, C.c_int, C.c_double, _VP, _VP, _VP,
+                                   C.c_double, C.c_int, _VP]),
+        "mg_op_resid_restrict": (C.c_int, [_VP, _P(mg_op_params), C.c_int, C.c_int, C.c_double, _VP, _VP, _VP,
+                                           _VP, _VP, _P(C.c_double), _P(C.c_double)]),
+        "mg_op_coarse_source": (C.c_int, [_VP, _P(mg_op_params), C.c_int, C.c_int, C.c_double, _VP, _VP, _VP,
+                                          _VP, _P(C.c_double)]),
+        "mg_op_prolong_add": (C.c_int, [_VP, C.c_int, C.c_int, _VP, _VP, _VP]),
+        "mg_op_coarsest": (C.c_int, [_VP, _P(mg_op_params), C.c_int, C.c_double, _VP, _VP, _VP, C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return sorted(sig)
+
+
+DECLARED = None
+
+
+def lib():
+    """The loaded library (raises ImportError if it is not built)."""
+    global _lib, DECLARED
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libmgglam.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+        _lib = C.CDLL(LIB_PATH)
+        DECLARED = _declare(_lib)
+    return _lib
+
+
+class MGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("mgglam error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _ptr(x):
+    """Raw data pointer of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("array arguments must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array arguments must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(x))
+
+
+def _check_dtype(x, kind):
+    if x is None:
+        return
+    name = str(getattr(x, "dtype", ""))
+    want = {"f64": ("float64", "torch.float64"), "f32": ("float32", "torch.float32"),
+            "i32": ("int32", "torch.int32")}[kind]
+    if name not in want:
+        raise TypeError("expected %s array, got %s" % (kind, name))
+
+
+def opts(**kw) -> mg_opts:
+    o = mg_opts()
+    lib().mg_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """An mg_ctx on one device; `stream` is a torch.cuda.Stream, a raw
+    cudaStream_t integer or None."""
+
+    def __init__(self, device: int = 0, stream=None):
+        raw = getattr(stream, "cuda_stream", stream)
+        h = C.c_void_p()
+        rc = lib().mg_ctx_create(C.byref(h), int(device), raw)
+        if rc != 0:
+            raise MGError(rc, "mg_ctx_create failed (device %d)" % device)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mg_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return lib().mg_last_error_string(self.h).decode()
+
+    def workspace_bytes(self) -> int:
+        return lib().mg_ctx_workspace_bytes(self.h)
+
+    def set_profiling(self, on: bool):
+        return self._rc(lib().mg_ctx_set_profiling(self.h, int(bool(on))))
+
+    def probe_alu_peaks(self):
+        """(FP64, FP32) FMA throughput in TFLOP/s measured on this device."""
+        a, b = C.c_double(), C.c_double()
+        self._rc(lib().mg_probe_alu_peaks(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def _rc(self, rc, allow_warn=True):
+        if rc < 0 or (rc > 0 and not allow_warn):
+            raise MGError(rc, self.last_error())
+        return rc
+
+
+def mg_ctx_create(device=0, stream=None) -> Context:
+    return Context(device, stream)
+
+
+def mg_ctx_destroy(ctx: Context):
+    ctx.close()
+
+
+def mg_solve_dgp(ctx: Context, instances, o: mg_opts = None):
+    """instances: list of dicts {ng, box_mpch, a, omega_m, rc_h0, delta, phi}.
+    Returns (rc, [mg_stats])."""
+    n = len(instances)
+    arr = (mg_instance * n)()
+    for q, d in enumerate(instances):
+        _check_dtype(d["delta"], "f64")
+        _check_dtype(d["phi"], "f64")
+        arr[q].g = mg_grid(int(d["ng"]), float(d.get("box_mpch", d["ng"])), float(d["a"]), float(d["omega_m"]))
+        arr[q].p = mg_dgp_params(float(d["rc_h0"]))
+        arr[q].delta = _ptr(d["delta"])
+        arr[q].phi = _ptr(d["phi"])
+    st = (mg_stats * n)()
+    rc = lib().mg_solve_dgp(ctx.h, n, arr, C.byref(o or opts()), st)
+    ctx._rc(rc)
+    return rc, list(st)
+
+
+def mg_solve_kmouflage(ctx: Context, ng, box_mpch, a, omega_m, n, k0, beta_kmo, lam, phibar_prime_over_h0, A_bar,
+                       delta, phi, o: mg_opts = None):
+    _check_dtype(delta, "f64")
+    _check_dtype(phi, "f64")
+    g = mg_grid(int(ng), float(box_mpch), float(a), float(omega_m))
+    p = mg_kmo_params(int(n), float(k0), float(beta_kmo), float(lam), float(phibar_prime_over_h0), float(A_bar))
+    st = mg_stats()
+    rc = lib().mg_solve_kmouflage(ctx.h, C.byref(g), C.byref(p), C.byref(o or opts()), _ptr(delta), _ptr(phi),
+                                  C.byref(st))
+    ctx._rc(rc)
+    return rc, st
+
+
+def pm_cic_deposit(ctx: Context, ng, pos, delta_out):
+    _check_dtype(pos, "f32")
+    _check_dtype(delta_out, "f64")
+    npart = int(pos.shape[0])
+    return ctx._rc(lib().pm_cic_deposit(ctx.h, int(ng), _ptr(pos), npart, _ptr(delta_out)))
+
+
+def pm_cic_index(ctx: Context, ng, pos, idx_out):
+    _check_dtype(pos, "f32")
+    _check_dtype(idx_out, "i32")
+    return ctx._rc(lib().pm_cic_index(ctx.h, int(ng), _ptr(pos), int(pos.shape[0]), _ptr(idx_out)))
+
+
+def pm_step(ctx: Context, state: pm_state, o: mg_opts = None):
+    st = mg_stats()
+    rc = lib().pm_step(ctx.h, C.byref(state), C.byref(o or opts()), C.byref(st))
+    ctx._rc(rc)
+    return rc, st
+
+
+def mg_solve_adjoint(ctx: Context, ng, box_mpch, a, omega_m, rc_h0, phi, delta, dL_dphi, dL_ddelta_out,
+                     o: mg_opts = None):
+    g = mg_grid(int(ng), float(box_mpch), float(a), float(omega_m))
+    p = mg_dgp_params(float(rc_h0))
+    drc = C.c_double(0.0)
+    st = mg_stats()
+    rc = lib().mg_solve_adjoint(ctx.h, C.byref(g), C.byref(p), C.byref(o or opts()), _ptr(phi), _ptr(delta),
+                                _ptr(dL_dphi), _ptr(dL_ddelta_out), C.cast(C.pointer(drc), C.c_void_p),
+                                C.byref(st))
+    ctx._rc(rc)
+    return rc, drc.value, st
+
+
+# ---------------------------------------------------------------- kernel level
+
+def op_params(model=0, alpha=0.0, nkmo=2, gamma=0.0, bterm=0.0):
+    return mg_op_params(int(model), float(alpha), int(nkmo), float(gamma), float(bterm))
+
+
+def mg_op_smooth(ctx, op, precision, n, h, u_in, s, f, c, colour, u_out):
+    return ctx._rc(lib().mg_op_smooth(ctx.h, C.byref(op), precision, n, h, _ptr(u_in), _ptr(s), _ptr(f), c,
+                                      colour, _ptr(u_out)))
+
+
+def mg_op_resid_restrict(ctx, op, precision, n, h, u, s, f, Ru, Rd):
+    c = C.c_double()
+    e = C.c_double()
+    ctx._rc(lib().mg_op_resid_restrict(ctx.h, C.byref(op), precision, n, h, _ptr(u), _ptr(s), _ptr(f), _ptr(Ru),
+                                       _ptr(Rd), C.byref(c), C.byref(e)))
+    return c.value, e.value
+
+
+def mg_op_coarse_source(ctx, op, precision, n, h, Ru, Rd, s, f_out):
+    c = C.c_double()
+    ctx._rc(lib().mg_op_coarse_source(ctx.h, C.byref(op), precision, n, h, _ptr(Ru), _ptr(Rd), _ptr(s),
+                                      _ptr(f_out), C.byref(c)))
+    return c.value
+
+
+def mg_op_prolong_add(ctx, precision, n, u_fine, uc, urc):
+    return ctx._rc(lib().mg_op_prolong_add(ctx.h, precision, n, _ptr(u_fine), _ptr(uc), _ptr(urc)))
+
+
+def mg_op_coarsest(ctx, op, n, h, u, s, f, sweeps):
+    return ctx._rc(lib().mg_op_coarsest(ctx.h, C.byref(op), n, h, _ptr(u), _ptr(s), _ptr(f), sweeps))

@@ -1,0 +1,244 @@
+// Shared device code of the GB300 MG-GLAM solvers (arXiv:2110.00566).
+//
+// Layout.  Every multigrid level of n^3 cells (n even) is stored
+// colour-split: cells with (i+j+k) even (colour 0) and odd (colour 1) live in
+// two arrays of n*n*(n/2) elements, index (i*n + j)*(n/2) + m with m = k/2.
+// In row (i, j) the cells of colour c sit at k = 2m + p, p = (c+i+j) & 1.
+// With this layout all 6 face neighbours of a colour-c cell are in the other
+// array and all 12 edge neighbours of the 19-point stencil are in the same
+// array; the rows (i+-1, j), (i, j+-1), (i+-1, j+-1) are read at the same m,
+// except the k+-1 neighbours, which sit at m + p and m + p - 1 (wrapped).
+// A half-sweep of one colour therefore reads both arrays and writes a third
+// (ping-pong for the updated colour), which makes the colour-simultaneous
+// update race-free; the centre value is never read by the smoother.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mg {
+
+// -------------------------------------------------------------------------
+// per-level scalars kept in device memory (FP64)
+// -------------------------------------------------------------------------
+struct LevScal {
+    double c;       // compatibility constant <N> used by the smoother
+    double fshift;  // constant part of the FAS source (f = f' + fshift)
+    double dc;      // c_new - c_old of the last residual pass
+    double eps2;    // mean d^2 of the last residual pass (with c_new)
+    double sumN;    // sum of N of the last residual pass
+    double clamps;  // sqrt clamps counted in the last residual pass
+    double mean;    // scratch mean (delta or u)
+    double aux;     // scratch
+};
+
+// reduction scratch shared by the reduction kernels of one pyramid
+struct RedBuf {
+    double *partials;       // [MAX_RED_BLOCKS * 4]
+    unsigned int *counter;  // one arrival counter, reset by the last block
+    int cap;                // blocks the partials buffer holds
+};
+constexpr int MAX_RED_BLOCKS = 4096;
+
+// -------------------------------------------------------------------------
+// operator parameters, with the h-dependent constants folded in on the host
+// -------------------------------------------------------------------------
+template <typename T>
+struct OpK {
+    int model;   // 0 nDGP, 1 Kmouflage
+    int nkmo;
+    T alpha, abs_alpha, sgn_alpha, alpha2, c83;  // nDGP
+    T k1, k2, k3;                                // Kmouflage: 1+gamma b^(n-1), (2n+1)gamma/3, 2(n-1)gamma
+};
+
+template <typename T>
+struct LevK {
+    int n, half;
+    T h2;        // h^2
+    T inv_h2;    // 1/h^2
+    T qd, qo;    // nDGP: 1/(3h^4), 1/(8h^4)
+    T td, to;    // Kmouflage: 1/(12h^4), 1/(8h^4)
+    T g2s;       // Kmouflage: 1/(4h^2)
+};
+
+template <typename T>
+__host__ __device__ inline LevK<T> make_levk(int n, double h)
+{
+    LevK<T> L{};
+    L.n = n;
+    L.half = n / 2;
+    const double h2 = h * h, h4 = h2 * h2;
+    L.h2 = (T)h2;
+    L.inv_h2 = (T)(1.0 / h2);
+    L.qd = (T)(1.0 / (3.0 * h4));
+    L.qo = (T)(1.0 / (8.0 * h4));
+    L.td = (T)(1.0 / (12.0 * h4));
+    L.to = (T)(1.0 / (8.0 * h4));
+    L.g2s = (T)(1.0 / (4.0 * h2));
+    return L;
+}
+
+// the 18 neighbours of the 19-point stencil
+template <typename T>
+struct Nb {
+    T xp, xm, yp, ym, zp, zm;          // faces
+    T xpyp, xmym, xpym, xmyp;          // xy edges
+    T xpzp, xmzm, xpzm, xmzp;          // xz edges
+    T ypzp, ymzm, ypzm, ymzp;          // yz edges
+};
+
+__device__ __forceinline__ int wrap_p(int i, int n) { return i + 1 == n ? 0 : i + 1; }
+__device__ __forceinline__ int wrap_m(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+
+__device__ __forceinline__ long long row_of(int i, int j, int n, int half)
+{
+    return ((long long)i * n + j) * half;
+}
+
+// Gather the 18 neighbours of the colour-c cell (i, j, m) whose row parity
+// is p = (c+i+j)&1.  S: array of colour c, O: array of the other colour.
+template <typename T>
+__device__ __forceinline__ void gather(Nb<T> &v, const T *__restrict__ S, const T *__restrict__ O,
+                                       int n, int half, int i, int j, int m, int p)
+{
+    const int ip = wrap_p(i, n), im = wrap_m(i, n), jp = wrap_p(j, n), jm = wrap_m(j, n);
+    int mp = m + p;
+    if (mp == half) mp = 0;
+    int mm = m - 1 + p;
+    if (mm < 0) mm = half - 1;
+    const long long r00 = row_of(i, j, n, half);
+    const long long rp0 = row_of(ip, j, n, half), rm0 = row_of(im, j, n, half);
+    const long long r0p = row_of(i, jp, n, half), r0m = row_of(i, jm, n, half);
+    v.xp = __ldg(O + rp0 + m);
+    v.xm = __ldg(O + rm0 + m);
+    v.yp = __ldg(O + r0p + m);
+    v.ym = __ldg(O + r0m + m);
+    v.zp = __ldg(O + r00 + mp);
+    v.zm = __ldg(O + r00 + mm);
+    v.xpyp = __ldg(S + row_of(ip, jp, n, half) + m);
+    v.xmym = __ldg(S + row_of(im, jm, n, half) + m);
+    v.xpym = __ldg(S + row_of(ip, jm, n, half) + m);
+    v.xmyp = __ldg(S + row_of(im, jp, n, half) + m);
+    v.xpzp = __ldg(S + rp0 + mp);
+    v.xmzm = __ldg(S + rm0 + mm);
+    v.xpzm = __ldg(S + rp0 + mm);
+    v.xmzp = __ldg(S + rm0 + mp);
+    v.ypzp = __ldg(S + r0p + mp);
+    v.ymzm = __ldg(S + r0m + mm);
+    v.ypzm = __ldg(S + r0p + mm);
+    v.ymzp = __ldg(S + r0m + mp);
+}
+
+template <typename T>
+__device__ __forceinline__ T ipow(T x, int p)
+{
+    T r = T(1);
+    for (int q = 0; q < p; ++q) r *= x;
+    return r;
+}
+
+// N(u) at a cell, the right-hand side of Lap u = N(u).
+//  nDGP (Sec. 3.2.3, Eq. DGP): Sigma = Q + s with
+//    Q = [(Sx-Sy)^2 + (Sx-Sz)^2 + (Sy-Sz)^2]/(3h^4) + (Cxy^2+Cxz^2+Cyz^2)/(8h^4)
+//  (the printed (2/3h^4)[Dxx^2+... - DxxDyy - ...] rewritten with
+//  D_aa - D_bb = S_a - S_b, which shows that Sigma has no centre term), and
+//    N = 2 sgn(alpha) Sigma / (|alpha| + sqrt(alpha^2 + 8 Sigma/3)),
+//  the rationalised form of (3/4)[-alpha + sgn(alpha) sqrt(...)]; a negative
+//  sqrt argument gives -(3/4) alpha and is counted.
+//  Kmouflage (Sec. 3.2.4, Eq. kmf_eqn_codeunit_final / c~):
+//    N = (s - 2(n-1) gamma (G^2)^(n-2) T) / (1 + gamma b^(n-1) + (2n+1)gamma/3 (G^2)^(n-1))
+template <typename T>
+__device__ __forceinline__ T op_N(const OpK<T> &op, const LevK<T> &L, const Nb<T> &v, T s, int &clamp)
+{
+    const T Sx = v.xp + v.xm, Sy = v.yp + v.ym, Sz = v.zp + v.zm;
+    const T Cxy = (v.xpyp + v.xmym) - (v.xpym + v.xmyp);
+    const T Cxz = (v.xpzp + v.xmzm) - (v.xpzm + v.xmzp);
+    const T Cyz = (v.ypzp + v.ymzm) - (v.ypzm + v.ymzp);
+    if (op.model == 0) {
+        const T a = Sx - Sy, b = Sx - Sz, c = Sy - Sz;
+        const T Q = (a * a + b * b + c * c) * L.qd + (Cxy * Cxy + Cxz * Cxz + Cyz * Cyz) * L.qo;
+        const T sig = Q + s;
+        const T arg = op.alpha2 + op.c83 * sig;
+        if (arg < T(0)) {
+            clamp = 1;
+            return T(-0.75) * op.alpha;
+        }
+        return T(2) * op.sgn_alpha * sig / (op.abs_alpha + sqrt(arg));
+    } else {
+        const T dx = v.xp - v.xm, dy = v.yp - v.ym, dz = v.zp - v.zm;
+        const T dx2 = dx * dx, dy2 = dy * dy, dz2 = dz * dz;
+        const T G2 = (dx2 + dy2 + dz2) * L.g2s;
+        const T Tt = (dx2 * (T(2) * Sx - Sy - Sz) + dy2 * (T(2) * Sy - Sx - Sz) + dz2 * (T(2) * Sz - Sx - Sy)) * L.td
+                   + (Cxy * dx * dy + Cxz * dx * dz + Cyz * dy * dz) * L.to;
+        const T pw2 = ipow(G2, op.nkmo - 2);
+        const T sigma1 = op.k1 + op.k2 * pw2 * G2;
+        return (s - op.k3 * pw2 * Tt) / sigma1;
+    }
+}
+
+// -------------------------------------------------------------------------
+// deterministic block reduction of NV doubles (warp shuffles, fixed order)
+// -------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *sh /* >= 32*NV */)
+{
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int lane = tid & 31, warp = tid >> 5, nwarps = (nthreads + 31) >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[warp * NV + q] = v[q];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            v[q] = lane < nwarps ? sh[lane * NV + q] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+        }
+    }
+}
+
+// Store this block's NV sums as partials; the block that arrives last sums
+// all partials in block order (so the result does not depend on scheduling)
+// and returns true in every one of its threads with the totals in tot[]
+// (valid in thread 0).  Blocks must be launched with >= 32 threads.
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], const RedBuf &rb, double (&tot)[NV])
+{
+    __shared__ double sh[32 * NV];
+    __shared__ bool last;
+    block_sum<NV>(v, sh);
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) rb.partials[(size_t)bid * NV + q] = v[q];
+        __threadfence();
+        const unsigned t = atomicAdd(rb.counter, 1u);
+        last = (t == nb - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+    // each thread sums a contiguous chunk in order, then the block tree
+    const unsigned per = (nb + nthreads - 1) / nthreads;
+    const unsigned b0 = tid * per, b1 = min(nb, b0 + per);
+    for (unsigned b = b0; b < b1; ++b)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(rb.partials + (size_t)b * NV + q);
+    block_sum<NV>(acc, sh);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] = acc[q];
+    if (tid == 0) *rb.counter = 0u;
+    return true;
+}
+
+}  // namespace mg

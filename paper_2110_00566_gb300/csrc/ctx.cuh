@@ -1,0 +1,133 @@
+// Host-side context of libmgglam.so: streams, workspace pyramids, staging
+// buffers and error reporting shared by the solver and particle-mesh units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/mgglam.h"
+#include "kernels.cuh"
+
+namespace mg {
+
+// A CUDA error inside the library is reported by returning MG_ERR_CUDA with
+// the failing call recorded in ctx->err.
+struct CudaFail {
+    int code;
+};
+
+#define MG_CK(call)                                                                                   \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) {                                                                      \
+            ::mg::fail_cuda(ctx, e_, #call, __FILE__, __LINE__);                                     \
+            throw ::mg::CudaFail{e_ == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA};       \
+        }                                                                                             \
+    } while (0)
+
+struct CycleKey {
+    std::vector<int> state;  // cur[] of every level before the cycle
+    int pre, post, cycle, coarse_sweeps, nlev, prof;
+    bool operator<(const CycleKey &o) const
+    {
+        return std::tie(state, pre, post, cycle, coarse_sweeps, nlev, prof) <
+               std::tie(o.state, o.pre, o.post, o.cycle, o.coarse_sweeps, o.nlev, o.prof);
+    }
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> post_state;
+    int nprof = 0;  // profiled smoother launches recorded in the graph
+};
+
+// One multigrid level pyramid for a finest size n0 in storage type T.
+template <typename T>
+struct Pyramid {
+    int n0 = 0, nlev = 0;
+    bool correction = false;           // arrays for the MIXED correction form
+    std::vector<LevArrays<T>> L;
+    LevScal *scal = nullptr;           // device [nlev]
+    OpK<T> *opT = nullptr;             // device operator (storage precision)
+    OpK<double> *opD = nullptr;        // device operator (FP64, coarsest)
+    RedBuf rb{};
+    void *block = nullptr;             // one allocation carved into the arrays
+    size_t bytes = 0;
+    std::map<CycleKey, GraphEntry> graphs;
+
+    std::vector<int> state() const
+    {
+        std::vector<int> s;
+        for (auto &l : L) {
+            s.push_back(l.cur[0]);
+            s.push_back(l.cur[1]);
+        }
+        return s;
+    }
+    void set_state(const std::vector<int> &s)
+    {
+        for (size_t q = 0; q < L.size(); ++q) {
+            L[q].cur[0] = s[2 * q];
+            L[q].cur[1] = s[2 * q + 1];
+        }
+    }
+};
+
+struct PmWork;  // particle-mesh workspace (pm.cu)
+
+struct ModelDesc {
+    int model;         // 0 nDGP, 1 Kmouflage
+    double alpha;
+    int nkmo;
+    double gamma, bterm;
+    double s_coef;     // s = s_coef (delta - <delta>)
+    double eref_coef;  // eps_ref = rms(eref_coef (delta - <delta>))
+};
+
+
+}  // namespace mg
+
+struct mg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;   // internal stream (all work, captures)
+    cudaStream_t ustream = nullptr;  // caller's stream (ordered around each call)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+    std::string err;
+    std::map<int, mg::Pyramid<double> *> p64;
+    std::map<int, mg::Pyramid<float> *> p32;
+    // staging for host pointers: grow-only device buffers
+    void *stage[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t stage_bytes[4] = {0, 0, 0, 0};
+    double *hpin = nullptr;          // pinned host scratch (64 doubles)
+    double *dscratch = nullptr;      // device scratch (64 doubles)
+    mg::RedBuf rb{};                 // reduction buffer for stand-alone reductions
+    mg::PmWork *pm = nullptr;
+    // profiling of the finest-level smoother (events recorded in the graphs)
+    int prof_on = 0;
+    int prof_k = 0;                  // launches bracketed in the current cycle
+    std::vector<cudaEvent_t> pev;    // pairs (start, stop)
+};
+
+namespace mg {
+
+void fail_cuda(mg_ctx *ctx, cudaError_t e, const char *call, const char *file, int line);
+int set_err(mg_ctx *ctx, int code, const char *fmt, ...);
+bool is_device_ptr(const void *p);
+// device view of a caller array: the pointer itself if it is on the device,
+// else staging slot `slot` filled from the host (if copy_in).
+void *stage_in(mg_ctx *ctx, int slot, const void *p, size_t bytes, bool copy_in);
+void stage_out(mg_ctx *ctx, void *host, const void *dev, size_t bytes);
+size_t level_count(int n);
+bool valid_ng(int n);
+template <typename T>
+Pyramid<T> *get_pyramid(mg_ctx *ctx, int n, bool correction);
+
+// entry/exit ordering with the caller's stream
+void enter(mg_ctx *ctx);
+void leave(mg_ctx *ctx);
+
+}  // namespace mg

@@ -1,0 +1,626 @@
+// Multigrid kernels of the GB300 MG-GLAM solvers (arXiv:2110.00566,
+// Sec. 3.2.1 for the FAS machinery, Sec. 3.2.3 / 3.2.4 for the operators).
+// Colour-split layout and the neighbour gather are described in common.cuh.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace mg {
+
+namespace {
+
+inline int np2(int x)
+{
+    int b = 1;
+    while (b < x) b <<= 1;
+    return b;
+}
+
+// 256-thread blocks over (m, j) rows of one colour array
+inline dim3 block_mj(int half)
+{
+    const int bx = std::min(32, np2(half));
+    return dim3(bx, 256 / bx, 1);
+}
+
+inline dim3 grid_mj(int half, int n, const dim3 &b, int z)
+{
+    return dim3((half + b.x - 1) / b.x, (n + b.y - 1) / b.y, z);
+}
+
+// z extent for reduction kernels: keep the block count <= MAX_RED_BLOCKS
+inline int red_z(const dim3 &g, int zmax, int cap)
+{
+    const long long per = (long long)g.x * g.y;
+    long long z = cap / std::max<long long>(per, 1);
+    return (int)std::max<long long>(1, std::min<long long>(z, zmax));
+}
+
+}  // namespace
+
+template <typename T>
+OpK<T> make_opk(int model, double alpha, int nkmo, double gamma, double bterm)
+{
+    OpK<T> o{};
+    o.model = model;
+    o.nkmo = nkmo;
+    o.alpha = (T)alpha;
+    o.abs_alpha = (T)(alpha < 0 ? -alpha : alpha);
+    o.sgn_alpha = (T)(alpha >= 0 ? 1.0 : -1.0);
+    o.alpha2 = (T)(alpha * alpha);
+    o.c83 = (T)(8.0 / 3.0);
+    double bp = 1.0;
+    for (int q = 0; q < nkmo - 1; ++q) bp *= bterm;
+    o.k1 = (T)(1.0 + gamma * bp);
+    o.k2 = (T)((2.0 * nkmo + 1.0) * gamma / 3.0);
+    o.k3 = (T)(2.0 * (nkmo - 1) * gamma);
+    return o;
+}
+
+// ---------------------------------------------------------------------------
+// smoother: one colour-simultaneous half-sweep (Eq. nonlinear_GS_DGP)
+//   u_new = (S6 - h^2 (N - c + f)) / 6,  f = f' + fshift
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_smooth(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un, const T *__restrict__ Sc,
+         const T *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<T> L, const OpK<T> *__restrict__ opp, int colour)
+{
+    const OpK<T> op = *opp;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = blockIdx.z;
+    if (m >= L.half || j >= L.n) return;
+    const int p = (colour + i + j) & 1;
+    Nb<T> v;
+    gather(v, Uc, Uo, L.n, L.half, i, j, m, p);
+    const long long idx = row_of(i, j, L.n, L.half) + m;
+    int cl = 0;
+    const T N = op_N(op, L, v, __ldg(Sc + idx), cl);
+    const T cf = (T)(sc->fshift - sc->c);
+    const T f = Fc ? __ldg(Fc + idx) : T(0);
+    const T S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
+    Un[idx] = (S6 - L.h2 * (N + f + cf)) * T(1.0 / 6.0);
+}
+
+template <typename T>
+void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, int colour, cudaStream_t st)
+{
+    const dim3 b = block_mj(L.half);
+    const dim3 g = grid_mj(L.half, L.n, b, L.n);
+    const int nb = 1 - L.cur[colour];
+    k_smooth<T><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], L.f[colour], L.sc,
+                                 make_levk<T>(L.n, L.h), op, colour);
+    Lw->cur[colour] = nb;
+}
+
+// ---------------------------------------------------------------------------
+// residual norm on one level (both colours):
+//   d = Lap u - N + c_old - f;  c_new = <N>;  d_true = d + (c_new - c_old)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_resid_norm(const T *__restrict__ U0, const T *__restrict__ U1, const T *__restrict__ S0,
+             const T *__restrict__ S1, const T *__restrict__ F0, const T *__restrict__ F1, LevScal *sc,
+             RedBuf rb, LevK<T> L, const OpK<T> *__restrict__ opp)
+{
+    const OpK<T> op = *opp;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const double c_old = sc->c;
+    const double cshift = c_old - sc->fshift;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (m < L.half && j < L.n) {
+        for (int iz = blockIdx.z; iz < 2 * L.n; iz += gridDim.z) {
+            const int col = iz & 1, i = iz >> 1;
+            const T *Sa = col ? U1 : U0;
+            const T *Oa = col ? U0 : U1;
+            const int p = (col + i + j) & 1;
+            Nb<T> v;
+            gather(v, Sa, Oa, L.n, L.half, i, j, m, p);
+            const long long idx = row_of(i, j, L.n, L.half) + m;
+            int cl = 0;
+            const T N = op_N(op, L, v, __ldg((col ? S1 : S0) + idx), cl);
+            const T u = __ldg(Sa + idx);
+            const T *Fa = col ? F1 : F0;
+            const T f = Fa ? __ldg(Fa + idx) : T(0);
+            const T S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
+            const T dT = (S6 - T(6) * u) * L.inv_h2 - N - f;
+            const double d = (double)dT + cshift;
+            acc[0] += (double)N;
+            acc[1] += d;
+            acc[2] += d * d;
+            acc[3] += (double)cl;
+        }
+    }
+    double tot[4];
+    if (grid_sum<4>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
+        const double cnt = (double)L.n * L.n * L.n;
+        const double c_new = tot[0] / cnt;
+        const double dc = c_new - c_old;
+        sc->c = c_new;
+        sc->dc = dc;
+        sc->eps2 = (tot[2] + 2.0 * dc * tot[1] + cnt * dc * dc) / cnt;
+        sc->sumN = tot[0];
+        sc->clamps = tot[3];
+    }
+}
+
+template <typename T>
+void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb, cudaStream_t st)
+{
+    const dim3 b = block_mj(L.half);
+    dim3 g = grid_mj(L.half, L.n, b, 1);
+    g.z = red_z(g, 2 * L.n, rb.cap);
+    k_resid_norm<T><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb,
+                                     make_levk<T>(L.n, L.h), op);
+}
+
+// ---------------------------------------------------------------------------
+// fused residual + FAS restriction, one thread per coarse cell (I, J, K):
+//   the 8 children (2I+a, 2J+b, 2K+c) sit at split index K of the fine rows
+//   (2I+a, 2J+b), colour (a+b+c)&1.  Writes R u (coarse u and ur) and
+//   R d_old (into the coarse f, completed by the coarse-source kernel).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_resid_restrict(const T *__restrict__ U0, const T *__restrict__ U1, const T *__restrict__ S0,
+                 const T *__restrict__ S1, const T *__restrict__ F0, const T *__restrict__ F1, LevScal *sc,
+                 RedBuf rb, LevK<T> L, const OpK<T> *__restrict__ opp, T *__restrict__ Uc0, T *__restrict__ Uc1,
+                 T *__restrict__ URc0, T *__restrict__ URc1, T *__restrict__ RDc0, T *__restrict__ RDc1)
+{
+    const OpK<T> op = *opp;
+    const int nc = L.n / 2, halfc = nc / 2;
+    const int K = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const double c_old = sc->c;
+    const double cshift = c_old - sc->fshift;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (K < nc && J < nc) {
+        for (int I = blockIdx.z; I < nc; I += gridDim.z) {
+            T su = T(0), sd = T(0);
+#pragma unroll
+            for (int ab = 0; ab < 4; ++ab) {
+                const int a = ab >> 1, b = ab & 1;
+                const int i = 2 * I + a, j = 2 * J + b;
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int col = (a + b + cc) & 1;
+                    const T *Sa = col ? U1 : U0;
+                    const T *Oa = col ? U0 : U1;
+                    Nb<T> v;
+                    gather(v, Sa, Oa, L.n, L.half, i, j, K, cc);
+                    const long long idx = row_of(i, j, L.n, L.half) + K;
+                    int cl = 0;
+                    const T N = op_N(op, L, v, __ldg((col ? S1 : S0) + idx), cl);
+                    const T u = __ldg(Sa + idx);
+                    const T *Fa = col ? F1 : F0;
+                    const T f = Fa ? __ldg(Fa + idx) : T(0);
+                    const T S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
+                    const T dT = (S6 - T(6) * u) * L.inv_h2 - N - f;
+                    const double d = (double)dT + cshift;
+                    acc[0] += (double)N;
+                    acc[1] += d;
+                    acc[2] += d * d;
+                    acc[3] += (double)cl;
+                    su += u;
+                    sd += dT;
+                }
+            }
+            const int C = (I + J + K) & 1;
+            const long long cidx = row_of(I, J, nc, halfc) + (K >> 1);
+            const T Ru = su * T(0.125);
+            const T Rd = sd * T(0.125) + (T)cshift;
+            (C ? Uc1 : Uc0)[cidx] = Ru;
+            (C ? URc1 : URc0)[cidx] = Ru;
+            (C ? RDc1 : RDc0)[cidx] = Rd;
+        }
+    }
+    double tot[4];
+    if (grid_sum<4>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
+        const double cnt = (double)L.n * L.n * L.n;
+        const double c_new = tot[0] / cnt;
+        const double dc = c_new - c_old;
+        sc->c = c_new;
+        sc->dc = dc;
+        sc->eps2 = (tot[2] + 2.0 * dc * tot[1] + cnt * dc * dc) / cnt;
+        sc->sumN = tot[0];
+        sc->clamps = tot[3];
+    }
+}
+
+template <typename T>
+void launch_resid_restrict(const LevArrays<T> &Lf, LevArrays<T> &Lc, const OpK<T> *op, const RedBuf &rb,
+                           cudaStream_t st)
+{
+    const int nc = Lf.n / 2;
+    const dim3 b = block_mj(nc);
+    dim3 g = grid_mj(nc, nc, b, 1);
+    g.z = red_z(g, nc, rb.cap);
+    k_resid_restrict<T><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb,
+                                         make_levk<T>(Lf.n, Lf.h), op, Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1],
+                                         Lc.f[0], Lc.f[1]);
+}
+
+// ---------------------------------------------------------------------------
+// coarse FAS source (Eq. general_pde_numerical_coarse), in place over R d:
+//   f' = Lap(Ru) - N(Ru) - (Rd_old + dc_fine);  c = fshift = <N(Ru)>
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_coarse_source(const T *__restrict__ UR0, const T *__restrict__ UR1, const T *__restrict__ S0,
+                const T *__restrict__ S1, T *F0, T *F1, const LevScal *scf, LevScal *scc, RedBuf rb, LevK<T> L,
+                const OpK<T> *__restrict__ opp)
+{
+    const OpK<T> op = *opp;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const T dcf = (T)scf->dc;
+    double acc[2] = {0.0, 0.0};
+    if (m < L.half && j < L.n) {
+        for (int iz = blockIdx.z; iz < 2 * L.n; iz += gridDim.z) {
+            const int col = iz & 1, i = iz >> 1;
+            const T *Sa = col ? UR1 : UR0;
+            const T *Oa = col ? UR0 : UR1;
+            const int p = (col + i + j) & 1;
+            Nb<T> v;
+            gather(v, Sa, Oa, L.n, L.half, i, j, m, p);
+            const long long idx = row_of(i, j, L.n, L.half) + m;
+            int cl = 0;
+            const T N = op_N(op, L, v, __ldg((col ? S1 : S0) + idx), cl);
+            const T u = __ldg(Sa + idx);
+            const T S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
+            T *Fa = col ? F1 : F0;
+            const T rd = Fa[idx];
+            Fa[idx] = (S6 - T(6) * u) * L.inv_h2 - N - (rd + dcf);
+            acc[0] += (double)N;
+            acc[1] += (double)cl;
+        }
+    }
+    double tot[2];
+    if (grid_sum<2>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
+        const double cnt = (double)L.n * L.n * L.n;
+        const double c = tot[0] / cnt;
+        scc->c = c;
+        scc->fshift = c;
+        scc->dc = 0.0;
+        scc->sumN = tot[0];
+        scc->clamps = tot[1];
+    }
+}
+
+template <typename T>
+void launch_coarse_source(const LevArrays<T> &Lf, const LevArrays<T> &Lc, const OpK<T> *op, const RedBuf &rb,
+                          cudaStream_t st)
+{
+    const dim3 b = block_mj(Lc.half);
+    dim3 g = grid_mj(Lc.half, Lc.n, b, 1);
+    g.z = red_z(g, 2 * Lc.n, rb.cap);
+    k_coarse_source<T><<<g, b, 0, st>>>(Lc.ur[0], Lc.ur[1], Lc.s[0], Lc.s[1], Lc.f[0], Lc.f[1], Lf.sc, Lc.sc, rb,
+                                        make_levk<T>(Lc.n, Lc.h), op);
+}
+
+// ---------------------------------------------------------------------------
+// prolongation + correction (Eq. solution_correction): u += P(uH - urH),
+// weights 27, 9, 3, 1 over 64 for the parent, face, edge and vertex cells
+// on the fine cell's side.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T coarse_e(const T *__restrict__ A0, const T *__restrict__ A1, const T *__restrict__ B0,
+                                      const T *__restrict__ B1, int I, int J, int K, int nc, int halfc)
+{
+    const long long q = row_of(I, J, nc, halfc) + (K >> 1);
+    return ((I + J + K) & 1) ? (__ldg(A1 + q) - __ldg(B1 + q)) : (__ldg(A0 + q) - __ldg(B0 + q));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_prolong(T *U0, T *U1, const T *__restrict__ UH0, const T *__restrict__ UH1, const T *__restrict__ RH0,
+          const T *__restrict__ RH1, int n)
+{
+    const int half = n / 2, nc = n / 2, halfc = nc / 2;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int iz = blockIdx.z;
+    const int col = iz & 1, i = iz >> 1;
+    if (m >= half || j >= n) return;
+    const int p = (col + i + j) & 1;
+    const int k = 2 * m + p;
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    const int I2 = (i & 1) ? (I + 1 == nc ? 0 : I + 1) : (I == 0 ? nc - 1 : I - 1);
+    const int J2 = (j & 1) ? (J + 1 == nc ? 0 : J + 1) : (J == 0 ? nc - 1 : J - 1);
+    const int K2 = (k & 1) ? (K + 1 == nc ? 0 : K + 1) : (K == 0 ? nc - 1 : K - 1);
+    const T e000 = coarse_e(UH0, UH1, RH0, RH1, I, J, K, nc, halfc);
+    const T e100 = coarse_e(UH0, UH1, RH0, RH1, I2, J, K, nc, halfc);
+    const T e010 = coarse_e(UH0, UH1, RH0, RH1, I, J2, K, nc, halfc);
+    const T e001 = coarse_e(UH0, UH1, RH0, RH1, I, J, K2, nc, halfc);
+    const T e110 = coarse_e(UH0, UH1, RH0, RH1, I2, J2, K, nc, halfc);
+    const T e101 = coarse_e(UH0, UH1, RH0, RH1, I2, J, K2, nc, halfc);
+    const T e011 = coarse_e(UH0, UH1, RH0, RH1, I, J2, K2, nc, halfc);
+    const T e111 = coarse_e(UH0, UH1, RH0, RH1, I2, J2, K2, nc, halfc);
+    const T corr = (T(27) * e000 + T(9) * (e100 + e010 + e001) + T(3) * (e110 + e101 + e011) + e111) * T(1.0 / 64.0);
+    T *Ua = col ? U1 : U0;
+    const long long idx = row_of(i, j, n, half) + m;
+    Ua[idx] += corr;
+}
+
+template <typename T>
+void launch_prolong(const LevArrays<T> &Lf, const LevArrays<T> &Lc, cudaStream_t st)
+{
+    const dim3 b = block_mj(Lf.half);
+    const dim3 g = grid_mj(Lf.half, Lf.n, b, 2 * Lf.n);
+    k_prolong<T><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], Lf.n);
+}
+
+// ---------------------------------------------------------------------------
+// coarsest level: one CTA, FP64 in shared memory (natural layout),
+// `sweeps` times { c = <N(u)>; colour 0; colour 1 }
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void gather_nat(Nb<double> &v, const double *u, int n, int i, int j, int k)
+{
+    const int ip = wrap_p(i, n), im = wrap_m(i, n), jp = wrap_p(j, n), jm = wrap_m(j, n);
+    const int kp = wrap_p(k, n), km = wrap_m(k, n);
+#define U_(a, b, c) u[((a) * n + (b)) * n + (c)]
+    v.xp = U_(ip, j, k); v.xm = U_(im, j, k);
+    v.yp = U_(i, jp, k); v.ym = U_(i, jm, k);
+    v.zp = U_(i, j, kp); v.zm = U_(i, j, km);
+    v.xpyp = U_(ip, jp, k); v.xmym = U_(im, jm, k); v.xpym = U_(ip, jm, k); v.xmyp = U_(im, jp, k);
+    v.xpzp = U_(ip, j, kp); v.xmzm = U_(im, j, km); v.xpzm = U_(ip, j, km); v.xmzp = U_(im, j, kp);
+    v.ypzp = U_(i, jp, kp); v.ymzm = U_(i, jm, km); v.ypzm = U_(i, jp, km); v.ymzp = U_(i, jm, kp);
+#undef U_
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_coarsest(T *U0, T *U1, const T *S0, const T *S1, const T *F0, const T *F1, LevScal *sc, int n, double h,
+           const OpK<double> *__restrict__ opp, int sweeps)
+{
+    const OpK<double> op = *opp;
+    extern __shared__ double smem[];
+    const int n3 = n * n * n, half = n / 2;
+    double *u = smem, *s = smem + n3, *f = smem + 2 * n3, *un = smem + 3 * n3;
+    __shared__ double shred[32];
+    __shared__ double cbc;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int q = tid; q < n3; q += nt) {
+        const int i = q / (n * n), j = (q / n) % n, k = q % n;
+        const int col = (i + j + k) & 1;
+        const long long si = row_of(i, j, n, half) + (k >> 1);
+        u[q] = (double)(col ? U1 : U0)[si];
+        s[q] = (double)(col ? S1 : S0)[si];
+        const T *Fa = col ? F1 : F0;
+        f[q] = Fa ? (double)Fa[si] : 0.0;
+    }
+    __syncthreads();
+    const LevK<double> L = make_levk<double>(n, h);
+    const double fshift = sc->fshift;
+    double c = sc->c;
+    for (int it = 0; it < sweeps; ++it) {
+        double acc[1] = {0.0};
+        for (int q = tid; q < n3; q += nt) {
+            Nb<double> v;
+            gather_nat(v, u, n, q / (n * n), (q / n) % n, q % n);
+            int cl = 0;
+            acc[0] += op_N(op, L, v, s[q], cl);
+        }
+        block_sum<1>(acc, shred);
+        if (tid == 0) cbc = acc[0] / n3;
+        __syncthreads();
+        c = cbc;
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int q = tid; q < n3; q += nt) {
+                const int i = q / (n * n), j = (q / n) % n, k = q % n;
+                if (((i + j + k) & 1) != colour) continue;
+                Nb<double> v;
+                gather_nat(v, u, n, i, j, k);
+                int cl = 0;
+                const double N = op_N(op, L, v, s[q], cl);
+                const double S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
+                un[q] = (S6 - L.h2 * (N - c + fshift + f[q])) * (1.0 / 6.0);
+            }
+            __syncthreads();
+            for (int q = tid; q < n3; q += nt) {
+                const int i = q / (n * n), j = (q / n) % n, k = q % n;
+                if (((i + j + k) & 1) == colour) u[q] = un[q];
+            }
+            __syncthreads();
+        }
+    }
+    for (int q = tid; q < n3; q += nt) {
+        const int i = q / (n * n), j = (q / n) % n, k = q % n;
+        const int col = (i + j + k) & 1;
+        const long long si = row_of(i, j, n, half) + (k >> 1);
+        (col ? U1 : U0)[si] = (T)u[q];
+    }
+    if (tid == 0) sc->c = c;
+}
+
+template <typename T>
+void launch_coarsest(const LevArrays<T> &L, const OpK<double> *op, int sweeps, cudaStream_t st)
+{
+    const int n3 = L.n * L.n * L.n;
+    const int threads = n3 <= 256 ? 256 : 512;
+    const size_t sm = sizeof(double) * 4 * n3;
+    k_coarsest<T><<<1, threads, sm, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, L.n, L.h, op,
+                                          sweeps);
+}
+
+// ---------------------------------------------------------------------------
+// plain restriction of a colour-split field (used for the density pyramid)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_restrict_plain(const T *__restrict__ F0, const T *__restrict__ F1, T *__restrict__ C0, T *__restrict__ C1, int nf)
+{
+    const int nc = nf / 2, halfc = nc / 2, halff = nf / 2;
+    const int K = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int I = blockIdx.z;
+    if (K >= nc || J >= nc) return;
+    T acc = T(0);
+#pragma unroll
+    for (int ab = 0; ab < 4; ++ab) {
+        const long long r = row_of(2 * I + (ab >> 1), 2 * J + (ab & 1), nf, halff) + K;
+        acc += __ldg(F0 + r) + __ldg(F1 + r);
+    }
+    const long long cidx = row_of(I, J, nc, halfc) + (K >> 1);
+    (((I + J + K) & 1) ? C1 : C0)[cidx] = acc * T(0.125);
+}
+
+template <typename T>
+void launch_restrict_plain(T *const fine[2], int nf, T *const coarse[2], cudaStream_t st)
+{
+    const int nc = nf / 2;
+    const dim3 b = block_mj(nc);
+    const dim3 g = grid_mj(nc, nc, b, nc);
+    k_restrict_plain<T><<<g, b, 0, st>>>(fine[0], fine[1], coarse[0], coarse[1], nf);
+}
+
+// ---------------------------------------------------------------------------
+// layout conversion, means
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_split(const double *__restrict__ nat, int n, T *__restrict__ D0, T *__restrict__ D1, double scale,
+        const double *__restrict__ mean)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = blockIdx.z;
+    if (k >= n || j >= n) return;
+    const double mu = mean ? *mean : 0.0;
+    const double x = nat[((long long)i * n + j) * n + k];
+    const long long si = row_of(i, j, n, n / 2) + (k >> 1);
+    (((i + j + k) & 1) ? D1 : D0)[si] = (T)(scale * (x - mu));
+}
+
+template <typename T>
+void launch_split(const double *nat, int n, T *const dst[2], double scale, const double *mean, cudaStream_t st)
+{
+    const dim3 b = block_mj(n);
+    const dim3 g = grid_mj(n, n, b, n);
+    k_split<T><<<g, b, 0, st>>>(nat, n, dst[0], dst[1], scale, mean);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_merge(const T *__restrict__ A0, const T *__restrict__ A1, int n, double *__restrict__ nat,
+        const double *__restrict__ mean)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = blockIdx.z;
+    if (k >= n || j >= n) return;
+    const double mu = mean ? *mean : 0.0;
+    const long long si = row_of(i, j, n, n / 2) + (k >> 1);
+    nat[((long long)i * n + j) * n + k] = (double)(((i + j + k) & 1) ? A1 : A0)[si] - mu;
+}
+
+template <typename T>
+void launch_merge(T *const src[2], int n, double *nat, const double *mean, cudaStream_t st)
+{
+    const dim3 b = block_mj(n);
+    const dim3 g = grid_mj(n, n, b, n);
+    k_merge<T><<<g, b, 0, st>>>(src[0], src[1], n, nat, mean);
+}
+
+__global__ void __launch_bounds__(256)
+k_mean_nat(const double *__restrict__ x, long long cnt, double *out, RedBuf rb)
+{
+    double acc[1] = {0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) acc[0] += x[q];
+    double tot[1];
+    if (grid_sum<1>(acc, rb, tot) && threadIdx.x == 0) *out = tot[0] / (double)cnt;
+}
+
+void launch_mean_nat(const double *x, long long cnt, double *out_mean, const RedBuf &rb, cudaStream_t st)
+{
+    const long long nb = std::min<long long>(MAX_RED_BLOCKS / 4, (cnt + 255) / 256);
+    k_mean_nat<<<(int)std::max<long long>(1, nb), 256, 0, st>>>(x, cnt, out_mean, rb);
+}
+
+__global__ void __launch_bounds__(256)
+k_rms_nat(const double *__restrict__ x, long long cnt, double scale, const double *__restrict__ mean, double *out,
+          RedBuf rb)
+{
+    double acc[1] = {0.0};
+    const double mu = mean ? *mean : 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
+        const double y = scale * (x[q] - mu);
+        acc[0] += y * y;
+    }
+    double tot[1];
+    if (grid_sum<1>(acc, rb, tot) && threadIdx.x == 0) *out = sqrt(tot[0] / (double)cnt);
+}
+
+void launch_rms_nat(const double *x, long long cnt, double scale, const double *mean, double *out, const RedBuf &rb,
+                    cudaStream_t st)
+{
+    const long long nb = std::min<long long>(MAX_RED_BLOCKS / 4, (cnt + 255) / 256);
+    k_rms_nat<<<(int)std::max<long long>(1, nb), 256, 0, st>>>(x, cnt, scale, mean, out, rb);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_mean_split(const T *__restrict__ A0, const T *__restrict__ A1, long long ncol, double *out, RedBuf rb)
+{
+    double acc[1] = {0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncol; q += stride)
+        acc[0] += (double)A0[q] + (double)A1[q];
+    double tot[1];
+    if (grid_sum<1>(acc, rb, tot) && threadIdx.x == 0) *out = tot[0] / (2.0 * (double)ncol);
+}
+
+template <typename T>
+void launch_mean_split(T *const a[2], long long ncol, double *out_mean, const RedBuf &rb, cudaStream_t st)
+{
+    const long long nb = std::min<long long>(MAX_RED_BLOCKS / 4, (ncol + 255) / 256);
+    k_mean_split<T><<<(int)std::max<long long>(1, nb), 256, 0, st>>>(a[0], a[1], ncol, out_mean, rb);
+}
+
+template <typename Td, typename Ts>
+__global__ void __launch_bounds__(256) k_convert(Td *D0, Td *D1, const Ts *S0, const Ts *S1, long long ncol)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncol; q += stride) {
+        D0[q] = (Td)S0[q];
+        D1[q] = (Td)S1[q];
+    }
+}
+
+template <typename Td, typename Ts>
+void launch_convert(Td *const dst[2], Ts *const src[2], long long ncol, cudaStream_t st)
+{
+    const long long nb = std::min<long long>(152 * 16, (ncol + 255) / 256);
+    k_convert<Td, Ts><<<(int)std::max<long long>(1, nb), 256, 0, st>>>(dst[0], dst[1], src[0], src[1], ncol);
+}
+
+void launch_fill_zero(void *p, size_t bytes, cudaStream_t st) { cudaMemsetAsync(p, 0, bytes, st); }
+
+// ---------------------------------------------------------------------------
+// explicit instantiations
+// ---------------------------------------------------------------------------
+#define INST(T)                                                                                              \
+    template OpK<T> make_opk<T>(int, double, int, double, double);                                         \
+    template void launch_smooth<T>(const LevArrays<T> &, LevArrays<T> *, const OpK<T> *, int, cudaStream_t); \
+    template void launch_resid_norm<T>(const LevArrays<T> &, const OpK<T> *, const RedBuf &, cudaStream_t);  \
+    template void launch_resid_restrict<T>(const LevArrays<T> &, LevArrays<T> &, const OpK<T> *,              \
+                                           const RedBuf &, cudaStream_t);                                   \
+    template void launch_coarse_source<T>(const LevArrays<T> &, const LevArrays<T> &, const OpK<T> *,         \
+                                          const RedBuf &, cudaStream_t);                                    \
+    template void launch_prolong<T>(const LevArrays<T> &, const LevArrays<T> &, cudaStream_t);               \
+    template void launch_coarsest<T>(const LevArrays<T> &, const OpK<double> *, int, cudaStream_t);          \
+    template void launch_restrict_plain<T>(T *const[2], int, T *const[2], cudaStream_t);                     \
+    template void launch_split<T>(const double *, int, T *const[2], double, const double *, cudaStream_t);   \
+    template void launch_merge<T>(T *const[2], int, double *, const double *, cudaStream_t);                 \
+    template void launch_mean_split<T>(T *const[2], long long, double *, const RedBuf &, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+template void launch_convert<float, double>(float *const[2], double *const[2], long long, cudaStream_t);
+template void launch_convert<double, float>(double *const[2], float *const[2], long long, cudaStream_t);
+
+}  // namespace mg

@@ -1,0 +1,63 @@
+// Launchers of the multigrid kernels (kernels.cu), templated on the storage
+// type T (double or float).  All launches go to the given stream.
+#pragma once
+#include "common.cuh"
+
+namespace mg {
+
+// arrays of one level, colour-split (index 0/1 = colour)
+template <typename T>
+struct LevArrays {
+    int n, half;
+    long long ncol;      // elements per colour array = n*n*n/2
+    double h;
+    T *u[2][2];          // [buffer][colour]
+    int cur[2];          // current buffer of each colour
+    T *s[2];             // density term
+    T *f[2];             // active FAS source f' (nullptr on a finest level)
+    T *fbuf[2];          // storage behind f
+    T *ur[2];            // R u saved for the correction
+    T *base[2];          // MIXED: base field of the correction operator
+    LevScal *sc;         // this level's device scalars
+    T *U(int colour) const { return u[cur[colour]][colour]; }
+};
+
+template <typename T> OpK<T> make_opk(int model, double alpha, int nkmo, double gamma, double bterm);
+
+template <typename T>
+void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, int colour, cudaStream_t st);
+template <typename T>
+void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb, cudaStream_t st);
+template <typename T>
+void launch_resid_restrict(const LevArrays<T> &Lf, LevArrays<T> &Lc, const OpK<T> *op, const RedBuf &rb,
+                           cudaStream_t st);
+template <typename T>
+void launch_coarse_source(const LevArrays<T> &Lf, const LevArrays<T> &Lc, const OpK<T> *op, const RedBuf &rb,
+                          cudaStream_t st);
+template <typename T>
+void launch_prolong(const LevArrays<T> &Lf, const LevArrays<T> &Lc, cudaStream_t st);
+template <typename T>
+void launch_coarsest(const LevArrays<T> &L, const OpK<double> *op, int sweeps, cudaStream_t st);
+template <typename T>
+void launch_restrict_plain(T *const fine[2], int nf, T *const coarse[2], cudaStream_t st);
+
+// natural FP64 <-> colour-split T
+template <typename T>
+void launch_split(const double *nat, int n, T *const dst[2], double scale, const double *mean, cudaStream_t st);
+template <typename T>
+void launch_merge(T *const src[2], int n, double *nat, const double *mean, cudaStream_t st);
+// mean of a natural FP64 array -> *out_mean (device)
+void launch_mean_nat(const double *x, long long cnt, double *out_mean, const RedBuf &rb, cudaStream_t st);
+// mean of a colour-split array -> *out_mean (device)
+template <typename T>
+void launch_mean_split(T *const a[2], long long ncol, double *out_mean, const RedBuf &rb, cudaStream_t st);
+// mean square of a natural FP64 array times scale^2 -> *out (device)
+void launch_rms_nat(const double *x, long long cnt, double scale, const double *mean, double *out, const RedBuf &rb,
+                    cudaStream_t st);
+
+// element-wise helpers on colour-split arrays
+template <typename Td, typename Ts>
+void launch_convert(Td *const dst[2], Ts *const src[2], long long ncol, cudaStream_t st);
+void launch_fill_zero(void *p, size_t bytes, cudaStream_t st);
+
+}  // namespace mg
