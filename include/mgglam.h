@@ -204,6 +204,13 @@ int pm_cic_deposit(mg_ctx *ctx, int ng, const float *pos, long long np,
 int pm_cic_index(mg_ctx *ctx, int ng, const float *pos, long long np,
                  int *idx_out);
 
+/* Newtonian potential on the mesh (Sec. 3.1; Eq. GR_poisson_codeunit):
+ * Lap Phi = (3/2) Omega_m a^-1 delta with the 7-point Laplacian, solved by
+ * FFT (cuFFT, FP64) with the Green's function -1/sum_d 4 sin^2(pi k_d/ng);
+ * the k = 0 mode is set to zero.  delta, phi_out: ng^3 FP64 (ng even). */
+int pm_newton_potential(mg_ctx *ctx, int ng, double a, double omega_m,
+                        const double *delta, double *phi_out);
+
 /*
  * Particle-mesh state for pm_step: positions x~ (FP32, np x 3, in [0, ng))
  * at scale factor a, momenta p~ (FP32, np x 3) at a - da/2 (at a itself
@@ -268,6 +275,15 @@ typedef struct {
 int mg_op_smooth(mg_ctx *ctx, const mg_op_params *op, int precision, int n,
                  double h, const double *u_in, const double *s, const double *f,
                  double c, int colour, double *u_out);
+
+/* The FP32 correction-form half-sweep used inside MG_PREC_MIXED: with a
+ * frozen base field b, the unknown correction e is updated on `colour` as
+ * e = (sum of face neighbours of e - h^2 (dN - c + f)) / 6 with
+ * dN = N(b + e) - N(b) evaluated without cancellation; the other colour is
+ * copied.  The same update as mg_op_smooth applied to u = b + e. */
+int mg_op_smooth_corr(mg_ctx *ctx, const mg_op_params *op, int n, double h,
+                      const double *e_in, const double *base, const double *s,
+                      const double *f, double c, int colour, double *e_out);
 
 /* Fused residual and FAS restriction (Sec. 3.2.1): with c_new = <N(u)>,
  * d = Lap u - N + c_new - f; writes R u and R d ((n/2)^3 each, 8-cell

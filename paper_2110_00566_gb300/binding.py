@@ -93,10 +93,13 @@ def _declare(L):
         "pm_cic_deposit": (C.c_int, [_VP, C.c_int, _VP, C.c_longlong, _VP]),
         "pm_cic_index": (C.c_int, [_VP, C.c_int, _VP, C.c_longlong, _VP]),
         "pm_step": (C.c_int, [_VP, _P(pm_state), _P(mg_opts), _P(mg_stats)]),
+        "pm_newton_potential": (C.c_int, [_VP, C.c_int, C.c_double, C.c_double, _VP, _VP]),
         "mg_solve_adjoint": (C.c_int, [_VP, _P(mg_grid), _P(mg_dgp_params), _P(mg_opts), _VP, _VP, _VP, _VP,
                                        _VP, _P(mg_stats)]),
         "mg_op_smooth": (C.c_int, [_VP, _P(mg_op_params), C.c_int, C.c_int, C.c_double, _VP, _VP, _VP,
                                    C.c_double, C.c_int, _VP]),
+        "mg_op_smooth_corr": (C.c_int, [_VP, _P(mg_op_params), C.c_int, C.c_double, _VP, _VP, _VP, _VP,
+                                        C.c_double, C.c_int, _VP]),
         "mg_op_resid_restrict": (C.c_int, [_VP, _P(mg_op_params), C.c_int, C.c_int, C.c_double, _VP, _VP, _VP,
                                            _VP, _VP, _P(C.c_double), _P(C.c_double)]),
         "mg_op_coarse_source": (C.c_int, [_VP, _P(mg_op_params), C.c_int, C.c_int, C.c_double, _VP, _VP, _VP,
@@ -262,6 +265,22 @@ def pm_cic_index(ctx: Context, ng, pos, idx_out):
     return ctx._rc(lib().pm_cic_index(ctx.h, int(ng), _ptr(pos), int(pos.shape[0]), _ptr(idx_out)))
 
 
+def pm_newton_potential(ctx: Context, ng, a, omega_m, delta, phi_out):
+    _check_dtype(delta, "f64")
+    _check_dtype(phi_out, "f64")
+    return ctx._rc(lib().pm_newton_potential(ctx.h, int(ng), float(a), float(omega_m), _ptr(delta),
+                                             _ptr(phi_out)))
+
+
+def make_pm_state(pos, mom, ng, box_mpch, omega_m, a, da, model=1, rc_h0=1.0, first=True, phi_ws=None):
+    """A pm_state over caller arrays (kept alive by the caller)."""
+    _check_dtype(pos, "f32")
+    _check_dtype(mom, "f32")
+    _check_dtype(phi_ws, "f64")
+    return pm_state(_ptr(pos), _ptr(mom), int(pos.shape[0]), int(ng), float(box_mpch), float(omega_m), float(a),
+                    float(da), int(model), int(bool(first)), mg_dgp_params(float(rc_h0)), _ptr(phi_ws))
+
+
 def pm_step(ctx: Context, state: pm_state, o: mg_opts = None):
     st = mg_stats()
     rc = lib().pm_step(ctx.h, C.byref(state), C.byref(o or opts()), C.byref(st))
@@ -291,6 +310,11 @@ def op_params(model=0, alpha=0.0, nkmo=2, gamma=0.0, bterm=0.0):
 def mg_op_smooth(ctx, op, precision, n, h, u_in, s, f, c, colour, u_out):
     return ctx._rc(lib().mg_op_smooth(ctx.h, C.byref(op), precision, n, h, _ptr(u_in), _ptr(s), _ptr(f), c,
                                       colour, _ptr(u_out)))
+
+
+def mg_op_smooth_corr(ctx, op, n, h, e_in, base, s, f, c, colour, e_out):
+    return ctx._rc(lib().mg_op_smooth_corr(ctx.h, C.byref(op), n, h, _ptr(e_in), _ptr(base), _ptr(s), _ptr(f), c,
+                                           colour, _ptr(e_out)))
 
 
 def mg_op_resid_restrict(ctx, op, precision, n, h, u, s, f, Ru, Rd):

@@ -128,6 +128,42 @@ __device__ __forceinline__ void gather(Nb<T> &v, const T *__restrict__ S, const 
     v.ymzp = __ldg(S + r0m + mp);
 }
 
+// the same 18 neighbours of two fields at once (unknown and base field)
+template <typename T>
+__device__ __forceinline__ void gather2(Nb<T> &v, Nb<T> &w, const T *__restrict__ S, const T *__restrict__ O,
+                                        const T *__restrict__ BS, const T *__restrict__ BO, int n, int half, int i,
+                                        int j, int m, int p)
+{
+    const int ip = wrap_p(i, n), im = wrap_m(i, n), jp = wrap_p(j, n), jm = wrap_m(j, n);
+    int mp = m + p;
+    if (mp == half) mp = 0;
+    int mm = m - 1 + p;
+    if (mm < 0) mm = half - 1;
+    const long long r00 = row_of(i, j, n, half);
+    const long long rp0 = row_of(ip, j, n, half), rm0 = row_of(im, j, n, half);
+    const long long r0p = row_of(i, jp, n, half), r0m = row_of(i, jm, n, half);
+    const long long rpp = row_of(ip, jp, n, half), rmm = row_of(im, jm, n, half);
+    const long long rpm = row_of(ip, jm, n, half), rmp = row_of(im, jp, n, half);
+    v.xp = __ldg(O + rp0 + m);   w.xp = __ldg(BO + rp0 + m);
+    v.xm = __ldg(O + rm0 + m);   w.xm = __ldg(BO + rm0 + m);
+    v.yp = __ldg(O + r0p + m);   w.yp = __ldg(BO + r0p + m);
+    v.ym = __ldg(O + r0m + m);   w.ym = __ldg(BO + r0m + m);
+    v.zp = __ldg(O + r00 + mp);  w.zp = __ldg(BO + r00 + mp);
+    v.zm = __ldg(O + r00 + mm);  w.zm = __ldg(BO + r00 + mm);
+    v.xpyp = __ldg(S + rpp + m); w.xpyp = __ldg(BS + rpp + m);
+    v.xmym = __ldg(S + rmm + m); w.xmym = __ldg(BS + rmm + m);
+    v.xpym = __ldg(S + rpm + m); w.xpym = __ldg(BS + rpm + m);
+    v.xmyp = __ldg(S + rmp + m); w.xmyp = __ldg(BS + rmp + m);
+    v.xpzp = __ldg(S + rp0 + mp); w.xpzp = __ldg(BS + rp0 + mp);
+    v.xmzm = __ldg(S + rm0 + mm); w.xmzm = __ldg(BS + rm0 + mm);
+    v.xpzm = __ldg(S + rp0 + mm); w.xpzm = __ldg(BS + rp0 + mm);
+    v.xmzp = __ldg(S + rm0 + mp); w.xmzp = __ldg(BS + rm0 + mp);
+    v.ypzp = __ldg(S + r0p + mp); w.ypzp = __ldg(BS + r0p + mp);
+    v.ymzm = __ldg(S + r0m + mm); w.ymzm = __ldg(BS + r0m + mm);
+    v.ypzm = __ldg(S + r0p + mm); w.ypzm = __ldg(BS + r0p + mm);
+    v.ymzp = __ldg(S + r0m + mp); w.ymzp = __ldg(BS + r0m + mp);
+}
+
 template <typename T>
 __device__ __forceinline__ T ipow(T x, int p)
 {
@@ -172,6 +208,96 @@ __device__ __forceinline__ T op_N(const OpK<T> &op, const LevK<T> &L, const Nb<T
         const T pw2 = ipow(G2, op.nkmo - 2);
         const T sigma1 = op.k1 + op.k2 * pw2 * G2;
         return (s - op.k3 * pw2 * Tt) / sigma1;
+    }
+}
+
+// dN = N(b + e) - N(b) at a cell, for the correction form of the mixed
+// precision solve: e (neighbours v) is the unknown correction, b (neighbours
+// w) the frozen base field.  Every difference is expanded so that no two
+// large terms cancel, which keeps the FP32 evaluation accurate relative to
+// the correction itself:
+//  nDGP: dSigma = sum_t t(e) (2 t(b) + t(e)) over the linear terms t of Q,
+//        dN = 2 sgn(alpha) dSigma / (r0 + r1), r = sqrt(alpha^2 + 8 Sigma/3)
+//        (from r1^2 - r0^2 = 8 dSigma / 3); a negative sqrt argument falls
+//        back to the clamped difference N1 - N0.
+//  Kmouflage: N = A/B with A = s - k3 G2^(n-2) T, B = k1 + k2 G2^(n-1):
+//        dN = (dA - N0 dB) / B1, where dG2, dT and the powers' differences
+//        are formed from products of the differenced linear terms.
+template <typename T>
+__device__ __forceinline__ T nd_clamped(const OpK<T> &op, T sig)
+{
+    const T arg = op.alpha2 + op.c83 * sig;
+    if (arg < T(0)) return T(-0.75) * op.alpha;
+    return T(2) * op.sgn_alpha * sig / (op.abs_alpha + sqrt(arg));
+}
+
+template <typename T>
+__device__ __forceinline__ T op_dN(const OpK<T> &op, const LevK<T> &L, const Nb<T> &v, const Nb<T> &w, T s,
+                                   int &clamp)
+{
+    const T eSx = v.xp + v.xm, eSy = v.yp + v.ym, eSz = v.zp + v.zm;
+    const T bSx = w.xp + w.xm, bSy = w.yp + w.ym, bSz = w.zp + w.zm;
+    const T eCxy = (v.xpyp + v.xmym) - (v.xpym + v.xmyp);
+    const T eCxz = (v.xpzp + v.xmzm) - (v.xpzm + v.xmzp);
+    const T eCyz = (v.ypzp + v.ymzm) - (v.ypzm + v.ymzp);
+    const T bCxy = (w.xpyp + w.xmym) - (w.xpym + w.xmyp);
+    const T bCxz = (w.xpzp + w.xmzm) - (w.xpzm + w.xmzp);
+    const T bCyz = (w.ypzp + w.ymzm) - (w.ypzm + w.ymzp);
+    if (op.model == 0) {
+        const T ea = eSx - eSy, eb = eSx - eSz, ec = eSy - eSz;
+        const T ba = bSx - bSy, bb = bSx - bSz, bc = bSy - bSz;
+        const T dQ = (ea * (T(2) * ba + ea) + eb * (T(2) * bb + eb) + ec * (T(2) * bc + ec)) * L.qd +
+                     (eCxy * (T(2) * bCxy + eCxy) + eCxz * (T(2) * bCxz + eCxz) + eCyz * (T(2) * bCyz + eCyz)) * L.qo;
+        const T Q0 = (ba * ba + bb * bb + bc * bc) * L.qd + (bCxy * bCxy + bCxz * bCxz + bCyz * bCyz) * L.qo;
+        const T sig0 = Q0 + s, sig1 = sig0 + dQ;
+        const T arg0 = op.alpha2 + op.c83 * sig0, arg1 = op.alpha2 + op.c83 * sig1;
+        if (arg0 < T(0) || arg1 < T(0)) {
+            clamp = 1;
+            return nd_clamped(op, sig1) - nd_clamped(op, sig0);
+        }
+        const T den = sqrt(arg0) + sqrt(arg1);
+        return den > T(0) ? T(2) * op.sgn_alpha * dQ / den : T(0);
+    } else {
+        const T edx = v.xp - v.xm, edy = v.yp - v.ym, edz = v.zp - v.zm;
+        const T bdx = w.xp - w.xm, bdy = w.yp - w.ym, bdz = w.zp - w.zm;
+        const T dx1 = bdx + edx, dy1 = bdy + edy, dz1 = bdz + edz;
+        const T bWx = T(2) * bSx - bSy - bSz, bWy = T(2) * bSy - bSx - bSz, bWz = T(2) * bSz - bSx - bSy;
+        const T eWx = T(2) * eSx - eSy - eSz, eWy = T(2) * eSy - eSx - eSz, eWz = T(2) * eSz - eSx - eSy;
+        const T qx = edx * (T(2) * bdx + edx), qy = edy * (T(2) * bdy + edy), qz = edz * (T(2) * bdz + edz);
+        const T G20 = (bdx * bdx + bdy * bdy + bdz * bdz) * L.g2s;
+        const T dG2 = (qx + qy + qz) * L.g2s;
+        const T G21 = G20 + dG2;
+        const T T0 = (bdx * bdx * bWx + bdy * bdy * bWy + bdz * bdz * bWz) * L.td +
+                     (bCxy * bdx * bdy + bCxz * bdx * bdz + bCyz * bdy * bdz) * L.to;
+        const T dTd = qx * (bWx + eWx) + bdx * bdx * eWx + qy * (bWy + eWy) + bdy * bdy * eWy + qz * (bWz + eWz) +
+                      bdz * bdz * eWz;
+        const T dTc = eCxy * dx1 * dy1 + bCxy * edx * dy1 + bCxy * bdx * edy + eCxz * dx1 * dz1 + bCxz * edx * dz1 +
+                      bCxz * bdx * edz + eCyz * dy1 * dz1 + bCyz * edy * dz1 + bCyz * bdy * edz;
+        const T dT = dTd * L.td + dTc * L.to;
+        const int nk = op.nkmo;
+        // G21^j G20^(m-1-j) summed over j: the factor of dG2 in G21^m - G20^m
+        T g_nm2 = T(0), g_nm1 = T(0);
+        {
+            T pa = T(1);
+            for (int jx = 0; jx <= nk - 2; ++jx) {
+                T pb = T(1);
+                for (int q = 0; q < nk - 2 - jx; ++q) pb *= G20;
+                g_nm1 += pa * pb;
+                pa *= G21;
+            }
+            pa = T(1);
+            for (int jx = 0; jx <= nk - 3; ++jx) {
+                T pb = T(1);
+                for (int q = 0; q < nk - 3 - jx; ++q) pb *= G20;
+                g_nm2 += pa * pb;
+                pa *= G21;
+            }
+        }
+        const T pw0 = ipow(G20, nk - 2), pw1 = ipow(G21, nk - 2);
+        const T dP = pw1 * dT + T0 * dG2 * g_nm2;
+        const T B0 = op.k1 + op.k2 * pw0 * G20, B1 = op.k1 + op.k2 * pw1 * G21;
+        const T N0 = (s - op.k3 * pw0 * T0) / B0;
+        return (-op.k3 * dP - N0 * op.k2 * dG2 * g_nm1) / B1;
     }
 }
 

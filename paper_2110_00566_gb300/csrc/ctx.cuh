@@ -99,9 +99,12 @@ struct mg_ctx {
     std::string err;
     std::map<int, mg::Pyramid<double> *> p64;
     std::map<int, mg::Pyramid<float> *> p32;
+    std::map<int, mg::Pyramid<double> *> p64c;  // correction-form pyramids
+    std::map<int, mg::Pyramid<float> *> p32c;
     // staging for host pointers: grow-only device buffers
-    void *stage[4] = {nullptr, nullptr, nullptr, nullptr};
-    size_t stage_bytes[4] = {0, 0, 0, 0};
+    static constexpr int NSTAGE = 6;
+    void *stage[NSTAGE] = {};
+    size_t stage_bytes[NSTAGE] = {};
     double *hpin = nullptr;          // pinned host scratch (64 doubles)
     double *dscratch = nullptr;      // device scratch (64 doubles)
     mg::RedBuf rb{};                 // reduction buffer for stand-alone reductions
@@ -129,5 +132,11 @@ Pyramid<T> *get_pyramid(mg_ctx *ctx, int n, bool correction);
 // entry/exit ordering with the caller's stream
 void enter(mg_ctx *ctx);
 void leave(mg_ctx *ctx);
+
+// nDGP solve on device arrays (validated options), and the CIC deposit
+int solve_dgp_dev(mg_ctx *ctx, int n, double a, double om, double rc, const double *delta, double *phi,
+                  const mg_opts &o, mg_stats *st);
+void cic_deposit_dev(mg_ctx *ctx, int ng, const float *pos, long long np, double *delta);
+int check_opts(mg_ctx *ctx, const mg_opts &o);
 
 }  // namespace mg

@@ -1,6 +1,8 @@
 // Multigrid kernels of the GB300 MG-GLAM solvers (arXiv:2110.00566,
 // Sec. 3.2.1 for the FAS machinery, Sec. 3.2.3 / 3.2.4 for the operators).
 // Colour-split layout and the neighbour gather are described in common.cuh.
+// Every stencil kernel comes in a plain form (N(u)) and a correction form
+// (CORR: N(b + e) - N(b) with a frozen base field b, see op_dN).
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -28,7 +30,8 @@ inline dim3 grid_mj(int half, int n, const dim3 &b, int z)
     return dim3((half + b.x - 1) / b.x, (n + b.y - 1) / b.y, z);
 }
 
-// z extent for reduction kernels: keep the block count <= MAX_RED_BLOCKS
+// z extent for reduction kernels: keep the block count within the
+// reduction buffer's capacity
 inline int red_z(const dim3 &g, int zmax, int cap)
 {
     const long long per = (long long)g.x * g.y;
@@ -57,14 +60,33 @@ OpK<T> make_opk(int model, double alpha, int nkmo, double gamma, double bterm)
     return o;
 }
 
+// N (plain) or dN (correction) at the colour-c cell (i, j, m) of row parity
+// p; also returns the sum of the 6 face neighbours of the unknown.
+template <typename T, bool CORR>
+__device__ __forceinline__ T cell_eval(const OpK<T> &op, const LevK<T> &L, const T *S, const T *O, const T *BS,
+                                       const T *BO, int i, int j, int m, int p, T s, int &cl, T &S6)
+{
+    Nb<T> v;
+    if (CORR) {
+        Nb<T> w;
+        gather2(v, w, S, O, BS, BO, L.n, L.half, i, j, m, p);
+        S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
+        return op_dN(op, L, v, w, s, cl);
+    }
+    gather(v, S, O, L.n, L.half, i, j, m, p);
+    S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
+    return op_N(op, L, v, s, cl);
+}
+
 // ---------------------------------------------------------------------------
 // smoother: one colour-simultaneous half-sweep (Eq. nonlinear_GS_DGP)
 //   u_new = (S6 - h^2 (N - c + f)) / 6,  f = f' + fshift
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool CORR>
 __global__ void __launch_bounds__(256)
 k_smooth(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un, const T *__restrict__ Sc,
-         const T *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<T> L, const OpK<T> *__restrict__ opp, int colour)
+         const T *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<T> L, const OpK<T> *__restrict__ opp,
+         int colour, const T *__restrict__ Bc, const T *__restrict__ Bo)
 {
     const OpK<T> op = *opp;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,14 +94,12 @@ k_smooth(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un,
     const int i = blockIdx.z;
     if (m >= L.half || j >= L.n) return;
     const int p = (colour + i + j) & 1;
-    Nb<T> v;
-    gather(v, Uc, Uo, L.n, L.half, i, j, m, p);
     const long long idx = row_of(i, j, L.n, L.half) + m;
     int cl = 0;
-    const T N = op_N(op, L, v, __ldg(Sc + idx), cl);
+    T S6;
+    const T N = cell_eval<T, CORR>(op, L, Uc, Uo, Bc, Bo, i, j, m, p, __ldg(Sc + idx), cl, S6);
     const T cf = (T)(sc->fshift - sc->c);
     const T f = Fc ? __ldg(Fc + idx) : T(0);
-    const T S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
     Un[idx] = (S6 - L.h2 * (N + f + cf)) * T(1.0 / 6.0);
 }
 
@@ -89,20 +109,27 @@ void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, in
     const dim3 b = block_mj(L.half);
     const dim3 g = grid_mj(L.half, L.n, b, L.n);
     const int nb = 1 - L.cur[colour];
-    k_smooth<T><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], L.f[colour], L.sc,
-                                 make_levk<T>(L.n, L.h), op, colour);
+    const LevK<T> K = make_levk<T>(L.n, L.h);
+    if (L.base[0])
+        k_smooth<T, true><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], L.f[colour],
+                                           L.sc, K, op, colour, L.base[colour], L.base[1 - colour]);
+    else
+        k_smooth<T, false><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour],
+                                            L.f[colour], L.sc, K, op, colour, nullptr, nullptr);
     Lw->cur[colour] = nb;
 }
 
 // ---------------------------------------------------------------------------
 // residual norm on one level (both colours):
 //   d = Lap u - N + c_old - f;  c_new = <N>;  d_true = d + (c_new - c_old)
+// optionally writes -d (old c) as FP32 for the correction solve's source
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool CORR>
 __global__ void __launch_bounds__(256)
 k_resid_norm(const T *__restrict__ U0, const T *__restrict__ U1, const T *__restrict__ S0,
              const T *__restrict__ S1, const T *__restrict__ F0, const T *__restrict__ F1, LevScal *sc,
-             RedBuf rb, LevK<T> L, const OpK<T> *__restrict__ opp)
+             RedBuf rb, LevK<T> L, const OpK<T> *__restrict__ opp, const T *__restrict__ B0,
+             const T *__restrict__ B1, float *__restrict__ D0, float *__restrict__ D1)
 {
     const OpK<T> op = *opp;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -116,17 +143,17 @@ k_resid_norm(const T *__restrict__ U0, const T *__restrict__ U1, const T *__rest
             const T *Sa = col ? U1 : U0;
             const T *Oa = col ? U0 : U1;
             const int p = (col + i + j) & 1;
-            Nb<T> v;
-            gather(v, Sa, Oa, L.n, L.half, i, j, m, p);
             const long long idx = row_of(i, j, L.n, L.half) + m;
             int cl = 0;
-            const T N = op_N(op, L, v, __ldg((col ? S1 : S0) + idx), cl);
+            T S6;
+            const T N = cell_eval<T, CORR>(op, L, Sa, Oa, col ? B1 : B0, col ? B0 : B1, i, j, m, p,
+                                           __ldg((col ? S1 : S0) + idx), cl, S6);
             const T u = __ldg(Sa + idx);
             const T *Fa = col ? F1 : F0;
             const T f = Fa ? __ldg(Fa + idx) : T(0);
-            const T S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
             const T dT = (S6 - T(6) * u) * L.inv_h2 - N - f;
             const double d = (double)dT + cshift;
+            if (D0) (col ? D1 : D0)[idx] = (float)(-d);
             acc[0] += (double)N;
             acc[1] += d;
             acc[2] += d * d;
@@ -147,13 +174,20 @@ k_resid_norm(const T *__restrict__ U0, const T *__restrict__ U1, const T *__rest
 }
 
 template <typename T>
-void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb, cudaStream_t st)
+void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb, cudaStream_t st,
+                       float *const *D)
 {
     const dim3 b = block_mj(L.half);
     dim3 g = grid_mj(L.half, L.n, b, 1);
     g.z = red_z(g, 2 * L.n, rb.cap);
-    k_resid_norm<T><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb,
-                                     make_levk<T>(L.n, L.h), op);
+    const LevK<T> K = make_levk<T>(L.n, L.h);
+    float *d0 = D ? D[0] : nullptr, *d1 = D ? D[1] : nullptr;
+    if (L.base[0])
+        k_resid_norm<T, true><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb, K, op,
+                                               L.base[0], L.base[1], d0, d1);
+    else
+        k_resid_norm<T, false><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb, K, op,
+                                                nullptr, nullptr, d0, d1);
 }
 
 // ---------------------------------------------------------------------------
@@ -162,12 +196,13 @@ void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb
 //   (2I+a, 2J+b), colour (a+b+c)&1.  Writes R u (coarse u and ur) and
 //   R d_old (into the coarse f, completed by the coarse-source kernel).
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool CORR>
 __global__ void __launch_bounds__(256)
 k_resid_restrict(const T *__restrict__ U0, const T *__restrict__ U1, const T *__restrict__ S0,
                  const T *__restrict__ S1, const T *__restrict__ F0, const T *__restrict__ F1, LevScal *sc,
                  RedBuf rb, LevK<T> L, const OpK<T> *__restrict__ opp, T *__restrict__ Uc0, T *__restrict__ Uc1,
-                 T *__restrict__ URc0, T *__restrict__ URc1, T *__restrict__ RDc0, T *__restrict__ RDc1)
+                 T *__restrict__ URc0, T *__restrict__ URc1, T *__restrict__ RDc0, T *__restrict__ RDc1,
+                 const T *__restrict__ B0, const T *__restrict__ B1)
 {
     const OpK<T> op = *opp;
     const int nc = L.n / 2, halfc = nc / 2;
@@ -188,15 +223,14 @@ k_resid_restrict(const T *__restrict__ U0, const T *__restrict__ U1, const T *__
                     const int col = (a + b + cc) & 1;
                     const T *Sa = col ? U1 : U0;
                     const T *Oa = col ? U0 : U1;
-                    Nb<T> v;
-                    gather(v, Sa, Oa, L.n, L.half, i, j, K, cc);
                     const long long idx = row_of(i, j, L.n, L.half) + K;
                     int cl = 0;
-                    const T N = op_N(op, L, v, __ldg((col ? S1 : S0) + idx), cl);
+                    T S6;
+                    const T N = cell_eval<T, CORR>(op, L, Sa, Oa, col ? B1 : B0, col ? B0 : B1, i, j, K, cc,
+                                                   __ldg((col ? S1 : S0) + idx), cl, S6);
                     const T u = __ldg(Sa + idx);
                     const T *Fa = col ? F1 : F0;
                     const T f = Fa ? __ldg(Fa + idx) : T(0);
-                    const T S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
                     const T dT = (S6 - T(6) * u) * L.inv_h2 - N - f;
                     const double d = (double)dT + cshift;
                     acc[0] += (double)N;
@@ -237,20 +271,26 @@ void launch_resid_restrict(const LevArrays<T> &Lf, LevArrays<T> &Lc, const OpK<T
     const dim3 b = block_mj(nc);
     dim3 g = grid_mj(nc, nc, b, 1);
     g.z = red_z(g, nc, rb.cap);
-    k_resid_restrict<T><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb,
-                                         make_levk<T>(Lf.n, Lf.h), op, Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1],
-                                         Lc.f[0], Lc.f[1]);
+    const LevK<T> K = make_levk<T>(Lf.n, Lf.h);
+    if (Lf.base[0])
+        k_resid_restrict<T, true><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb,
+                                                   K, op, Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], Lc.fbuf[0],
+                                                   Lc.fbuf[1], Lf.base[0], Lf.base[1]);
+    else
+        k_resid_restrict<T, false><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc,
+                                                    rb, K, op, Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], Lc.fbuf[0],
+                                                    Lc.fbuf[1], nullptr, nullptr);
 }
 
 // ---------------------------------------------------------------------------
 // coarse FAS source (Eq. general_pde_numerical_coarse), in place over R d:
 //   f' = Lap(Ru) - N(Ru) - (Rd_old + dc_fine);  c = fshift = <N(Ru)>
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool CORR>
 __global__ void __launch_bounds__(256)
 k_coarse_source(const T *__restrict__ UR0, const T *__restrict__ UR1, const T *__restrict__ S0,
                 const T *__restrict__ S1, T *F0, T *F1, const LevScal *scf, LevScal *scc, RedBuf rb, LevK<T> L,
-                const OpK<T> *__restrict__ opp)
+                const OpK<T> *__restrict__ opp, const T *__restrict__ B0, const T *__restrict__ B1)
 {
     const OpK<T> op = *opp;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -263,13 +303,12 @@ k_coarse_source(const T *__restrict__ UR0, const T *__restrict__ UR1, const T *_
             const T *Sa = col ? UR1 : UR0;
             const T *Oa = col ? UR0 : UR1;
             const int p = (col + i + j) & 1;
-            Nb<T> v;
-            gather(v, Sa, Oa, L.n, L.half, i, j, m, p);
             const long long idx = row_of(i, j, L.n, L.half) + m;
             int cl = 0;
-            const T N = op_N(op, L, v, __ldg((col ? S1 : S0) + idx), cl);
+            T S6;
+            const T N = cell_eval<T, CORR>(op, L, Sa, Oa, col ? B1 : B0, col ? B0 : B1, i, j, m, p,
+                                           __ldg((col ? S1 : S0) + idx), cl, S6);
             const T u = __ldg(Sa + idx);
-            const T S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
             T *Fa = col ? F1 : F0;
             const T rd = Fa[idx];
             Fa[idx] = (S6 - T(6) * u) * L.inv_h2 - N - (rd + dcf);
@@ -296,8 +335,13 @@ void launch_coarse_source(const LevArrays<T> &Lf, const LevArrays<T> &Lc, const 
     const dim3 b = block_mj(Lc.half);
     dim3 g = grid_mj(Lc.half, Lc.n, b, 1);
     g.z = red_z(g, 2 * Lc.n, rb.cap);
-    k_coarse_source<T><<<g, b, 0, st>>>(Lc.ur[0], Lc.ur[1], Lc.s[0], Lc.s[1], Lc.f[0], Lc.f[1], Lf.sc, Lc.sc, rb,
-                                        make_levk<T>(Lc.n, Lc.h), op);
+    const LevK<T> K = make_levk<T>(Lc.n, Lc.h);
+    if (Lc.base[0])
+        k_coarse_source<T, true><<<g, b, 0, st>>>(Lc.ur[0], Lc.ur[1], Lc.s[0], Lc.s[1], Lc.fbuf[0], Lc.fbuf[1], Lf.sc,
+                                                  Lc.sc, rb, K, op, Lc.base[0], Lc.base[1]);
+    else
+        k_coarse_source<T, false><<<g, b, 0, st>>>(Lc.ur[0], Lc.ur[1], Lc.s[0], Lc.s[1], Lc.fbuf[0], Lc.fbuf[1],
+                                                   Lf.sc, Lc.sc, rb, K, op, nullptr, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -370,15 +414,31 @@ __device__ __forceinline__ void gather_nat(Nb<double> &v, const double *u, int n
 #undef U_
 }
 
-template <typename T>
+template <bool CORR>
+__device__ __forceinline__ double nat_eval(const OpK<double> &op, const LevK<double> &L, const double *u,
+                                           const double *bs, int n, int i, int j, int k, double s, double &S6)
+{
+    Nb<double> v;
+    gather_nat(v, u, n, i, j, k);
+    S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
+    int cl = 0;
+    if (CORR) {
+        Nb<double> w;
+        gather_nat(w, bs, n, i, j, k);
+        return op_dN(op, L, v, w, s, cl);
+    }
+    return op_N(op, L, v, s, cl);
+}
+
+template <typename T, bool CORR>
 __global__ void __launch_bounds__(512)
 k_coarsest(T *U0, T *U1, const T *S0, const T *S1, const T *F0, const T *F1, LevScal *sc, int n, double h,
-           const OpK<double> *__restrict__ opp, int sweeps)
+           const OpK<double> *__restrict__ opp, int sweeps, const T *B0, const T *B1)
 {
     const OpK<double> op = *opp;
     extern __shared__ double smem[];
     const int n3 = n * n * n, half = n / 2;
-    double *u = smem, *s = smem + n3, *f = smem + 2 * n3, *un = smem + 3 * n3;
+    double *u = smem, *s = smem + n3, *f = smem + 2 * n3, *un = smem + 3 * n3, *bs = smem + 4 * n3;
     __shared__ double shred[32];
     __shared__ double cbc;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -390,6 +450,7 @@ k_coarsest(T *U0, T *U1, const T *S0, const T *S1, const T *F0, const T *F1, Lev
         s[q] = (double)(col ? S1 : S0)[si];
         const T *Fa = col ? F1 : F0;
         f[q] = Fa ? (double)Fa[si] : 0.0;
+        if (CORR) bs[q] = (double)(col ? B1 : B0)[si];
     }
     __syncthreads();
     const LevK<double> L = make_levk<double>(n, h);
@@ -398,10 +459,8 @@ k_coarsest(T *U0, T *U1, const T *S0, const T *S1, const T *F0, const T *F1, Lev
     for (int it = 0; it < sweeps; ++it) {
         double acc[1] = {0.0};
         for (int q = tid; q < n3; q += nt) {
-            Nb<double> v;
-            gather_nat(v, u, n, q / (n * n), (q / n) % n, q % n);
-            int cl = 0;
-            acc[0] += op_N(op, L, v, s[q], cl);
+            double S6;
+            acc[0] += nat_eval<CORR>(op, L, u, bs, n, q / (n * n), (q / n) % n, q % n, s[q], S6);
         }
         block_sum<1>(acc, shred);
         if (tid == 0) cbc = acc[0] / n3;
@@ -411,11 +470,8 @@ k_coarsest(T *U0, T *U1, const T *S0, const T *S1, const T *F0, const T *F1, Lev
             for (int q = tid; q < n3; q += nt) {
                 const int i = q / (n * n), j = (q / n) % n, k = q % n;
                 if (((i + j + k) & 1) != colour) continue;
-                Nb<double> v;
-                gather_nat(v, u, n, i, j, k);
-                int cl = 0;
-                const double N = op_N(op, L, v, s[q], cl);
-                const double S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
+                double S6;
+                const double N = nat_eval<CORR>(op, L, u, bs, n, i, j, k, s[q], S6);
                 un[q] = (S6 - L.h2 * (N - c + fshift + f[q])) * (1.0 / 6.0);
             }
             __syncthreads();
@@ -440,13 +496,17 @@ void launch_coarsest(const LevArrays<T> &L, const OpK<double> *op, int sweeps, c
 {
     const int n3 = L.n * L.n * L.n;
     const int threads = n3 <= 256 ? 256 : 512;
-    const size_t sm = sizeof(double) * 4 * n3;
-    k_coarsest<T><<<1, threads, sm, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, L.n, L.h, op,
-                                          sweeps);
+    const size_t sm = sizeof(double) * 5 * n3;
+    if (L.base[0])
+        k_coarsest<T, true><<<1, threads, sm, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, L.n, L.h,
+                                                    op, sweeps, L.base[0], L.base[1]);
+    else
+        k_coarsest<T, false><<<1, threads, sm, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, L.n, L.h,
+                                                     op, sweeps, nullptr, nullptr);
 }
 
 // ---------------------------------------------------------------------------
-// plain restriction of a colour-split field (used for the density pyramid)
+// plain restriction of a colour-split field (density and base pyramids)
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -477,7 +537,7 @@ void launch_restrict_plain(T *const fine[2], int nf, T *const coarse[2], cudaStr
 }
 
 // ---------------------------------------------------------------------------
-// layout conversion, means
+// layout conversion, means, element-wise helpers
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -598,7 +658,35 @@ void launch_convert(Td *const dst[2], Ts *const src[2], long long ncol, cudaStre
     k_convert<Td, Ts><<<(int)std::max<long long>(1, nb), 256, 0, st>>>(dst[0], dst[1], src[0], src[1], ncol);
 }
 
-void launch_fill_zero(void *p, size_t bytes, cudaStream_t st) { cudaMemsetAsync(p, 0, bytes, st); }
+__global__ void __launch_bounds__(256)
+k_add_correction(double *U0, double *U1, const float *__restrict__ E0, const float *__restrict__ E1, long long ncol)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncol; q += stride) {
+        U0[q] += (double)E0[q];
+        U1[q] += (double)E1[q];
+    }
+}
+
+void launch_add_correction(double *const U[2], float *const E[2], long long ncol, cudaStream_t st)
+{
+    const long long nb = std::min<long long>(152 * 16, (ncol + 255) / 256);
+    k_add_correction<<<(int)std::max<long long>(1, nb), 256, 0, st>>>(U[0], U[1], E[0], E[1], ncol);
+}
+
+__global__ void k_set_corr_scalars(LevScal *sc32, const LevScal *__restrict__ sc64, int nlev)
+{
+    const int l = threadIdx.x;
+    if (l >= nlev) return;
+    LevScal z{};
+    if (l == 0) z.fshift = -sc64->dc;
+    sc32[l] = z;
+}
+
+void launch_set_corr_scalars(LevScal *sc32, const LevScal *sc64, int nlev32, cudaStream_t st)
+{
+    k_set_corr_scalars<<<1, 32, 0, st>>>(sc32, sc64, nlev32);
+}
 
 // ---------------------------------------------------------------------------
 // explicit instantiations
@@ -606,7 +694,8 @@ void launch_fill_zero(void *p, size_t bytes, cudaStream_t st) { cudaMemsetAsync(
 #define INST(T)                                                                                              \
     template OpK<T> make_opk<T>(int, double, int, double, double);                                         \
     template void launch_smooth<T>(const LevArrays<T> &, LevArrays<T> *, const OpK<T> *, int, cudaStream_t); \
-    template void launch_resid_norm<T>(const LevArrays<T> &, const OpK<T> *, const RedBuf &, cudaStream_t);  \
+    template void launch_resid_norm<T>(const LevArrays<T> &, const OpK<T> *, const RedBuf &, cudaStream_t,   \
+                                       float *const *);                                                     \
     template void launch_resid_restrict<T>(const LevArrays<T> &, LevArrays<T> &, const OpK<T> *,              \
                                            const RedBuf &, cudaStream_t);                                   \
     template void launch_coarse_source<T>(const LevArrays<T> &, const LevArrays<T> &, const OpK<T> *,         \

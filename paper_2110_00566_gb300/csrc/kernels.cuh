@@ -1,5 +1,8 @@
 // Launchers of the multigrid kernels (kernels.cu), templated on the storage
-// type T (double or float).  All launches go to the given stream.
+// type T (double or float).  All launches go to the given stream.  A level
+// whose base[] arrays are set runs the correction form (unknown e, frozen
+// base field b, operator N(b + e) - N(b)) used inside the mixed-precision
+// solve; otherwise the plain operator N(u).
 #pragma once
 #include "common.cuh"
 
@@ -17,7 +20,7 @@ struct LevArrays {
     T *f[2];             // active FAS source f' (nullptr on a finest level)
     T *fbuf[2];          // storage behind f
     T *ur[2];            // R u saved for the correction
-    T *base[2];          // MIXED: base field of the correction operator
+    T *base[2];          // correction form: base field (nullptr: plain form)
     LevScal *sc;         // this level's device scalars
     T *U(int colour) const { return u[cur[colour]][colour]; }
 };
@@ -26,8 +29,11 @@ template <typename T> OpK<T> make_opk(int model, double alpha, int nkmo, double 
 
 template <typename T>
 void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, int colour, cudaStream_t st);
+// residual norm; with D set also writes -d (with the old c) as FP32,
+// colour-split
 template <typename T>
-void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb, cudaStream_t st);
+void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb, cudaStream_t st,
+                       float *const *D = nullptr);
 template <typename T>
 void launch_resid_restrict(const LevArrays<T> &Lf, LevArrays<T> &Lc, const OpK<T> *op, const RedBuf &rb,
                            cudaStream_t st);
@@ -51,13 +57,17 @@ void launch_mean_nat(const double *x, long long cnt, double *out_mean, const Red
 // mean of a colour-split array -> *out_mean (device)
 template <typename T>
 void launch_mean_split(T *const a[2], long long ncol, double *out_mean, const RedBuf &rb, cudaStream_t st);
-// mean square of a natural FP64 array times scale^2 -> *out (device)
+// rms of scale * (x - mean) for a natural FP64 array -> *out (device)
 void launch_rms_nat(const double *x, long long cnt, double scale, const double *mean, double *out, const RedBuf &rb,
                     cudaStream_t st);
 
 // element-wise helpers on colour-split arrays
 template <typename Td, typename Ts>
 void launch_convert(Td *const dst[2], Ts *const src[2], long long ncol, cudaStream_t st);
-void launch_fill_zero(void *p, size_t bytes, cudaStream_t st);
+// U += (double) E
+void launch_add_correction(double *const U[2], float *const E[2], long long ncol, cudaStream_t st);
+// correction pyramid scalars: all zero except fshift of level 0 = -dc of
+// the FP64 defect pass (the defect's compatibility shift)
+void launch_set_corr_scalars(LevScal *sc32, const LevScal *sc64, int nlev32, cudaStream_t st);
 
 }  // namespace mg

@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <cufft.h>
+
 #include "ctx.cuh"
 
 namespace mg {
@@ -81,13 +83,162 @@ static int grid1(long long n) { return (int)std::max<long long>(1, std::min<long
 struct PmWork {
     unsigned long long *acc = nullptr;
     size_t acc_bytes = 0;
+    // Poisson solve for one mesh size
+    int fft_n = 0;
+    cufftHandle fwd = 0, inv = 0;
+    double *rho = nullptr, *phin = nullptr, *phi = nullptr, *table = nullptr;
+    cufftDoubleComplex *spec = nullptr;
 };
+
+// 4 sin^2(pi k / n): minus the eigenvalues of the 1D 3-point Laplacian
+__global__ void k_lap_table(double *t, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        const double s = sinpi((double)k / (double)n);
+        t[k] = 4.0 * s * s;
+    }
+}
+
+// Green's function of the 7-point Laplacian on the rfft grid (n, n, n/2+1):
+// Phi_k = scale * rho_k / (-(t[i] + t[j] + t[kz])), zero mode set to 0.
+__global__ void __launch_bounds__(256)
+k_green(cufftDoubleComplex *spec, int n, const double *__restrict__ t, double scale)
+{
+    const int nz = n / 2 + 1;
+    const long long total = (long long)n * n * nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += stride) {
+        const int kz = (int)(q % nz);
+        const long long r = q / nz;
+        const int j = (int)(r % n), i = (int)(r / n);
+        const double lam = -(t[i] + t[j] + t[kz]);
+        cufftDoubleComplex v = spec[q];
+        if (q == 0) {
+            v.x = 0.0;
+            v.y = 0.0;
+        } else {
+            const double f = scale / lam;
+            v.x *= f;
+            v.y *= f;
+        }
+        spec[q] = v;
+    }
+}
+
+// -grad Phi by 3-point differences at the 8 CIC cells, interpolated with the
+// CIC weights, then the leapfrog kick and drift (code units of Sec. 3.1.1):
+//   p += g ck,  x += p cd,  wrap into [0, ng).  Phi = PhiN + 0.5 phi when phi
+// is given (Eq. poisson_nDGP).  Rounded as written (no contraction).
+__device__ __forceinline__ double pot(const double *__restrict__ A, const double *__restrict__ Bp, long long q)
+{
+    const double a = __ldg(A + q);
+    return Bp ? __dadd_rn(a, __dmul_rn(0.5, __ldg(Bp + q))) : a;
+}
+
+__global__ void __launch_bounds__(256)
+k_kick_drift(float *__restrict__ pos, float *__restrict__ mom, long long np, int ng, const double *__restrict__ phin,
+             const double *__restrict__ phi, double ck, double cd)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np; p += stride) {
+        int i0[3], i1[3];
+        double w0[3], w1[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) cic_axis(pos[3 * p + d], ng, i0[d], i1[d], w0[d], w1[d]);
+        double g[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int c = 0; c < 2; ++c) {
+                    const double w = __dmul_rn(__dmul_rn(a ? w1[0] : w0[0], b ? w1[1] : w0[1]), c ? w1[2] : w0[2]);
+                    const int i = a ? i1[0] : i0[0], j = b ? i1[1] : i0[1], k = c ? i1[2] : i0[2];
+                    const int ip = i + 1 == ng ? 0 : i + 1, im = i == 0 ? ng - 1 : i - 1;
+                    const int jp = j + 1 == ng ? 0 : j + 1, jm = j == 0 ? ng - 1 : j - 1;
+                    const int kp = k + 1 == ng ? 0 : k + 1, km = k == 0 ? ng - 1 : k - 1;
+                    auto I3 = [ng](int x, int y, int z) { return ((long long)x * ng + y) * ng + z; };
+                    const double gx = -__dsub_rn(pot(phin, phi, I3(ip, j, k)), pot(phin, phi, I3(im, j, k))) / 2.0;
+                    const double gy = -__dsub_rn(pot(phin, phi, I3(i, jp, k)), pot(phin, phi, I3(i, jm, k))) / 2.0;
+                    const double gz = -__dsub_rn(pot(phin, phi, I3(i, j, kp)), pot(phin, phi, I3(i, j, km))) / 2.0;
+                    g[0] = __dadd_rn(g[0], __dmul_rn(w, gx));
+                    g[1] = __dadd_rn(g[1], __dmul_rn(w, gy));
+                    g[2] = __dadd_rn(g[2], __dmul_rn(w, gz));
+                }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float pn = (float)__dadd_rn((double)mom[3 * p + d], __dmul_rn(g[d], ck));
+            mom[3 * p + d] = pn;
+            float x = (float)__dadd_rn((double)pos[3 * p + d], __dmul_rn((double)pn, cd));
+            if (x < 0.f) x = __fadd_rn(x, (float)ng);
+            if (x >= (float)ng) x = __fsub_rn(x, (float)ng);
+            pos[3 * p + d] = x;
+        }
+    }
+}
 
 static PmWork &pmw(mg_ctx *ctx)
 {
     if (!ctx->pm) ctx->pm = new PmWork();
     return *ctx->pm;
 }
+
+#define MG_CUFFT(call)                                                                               \
+    do {                                                                                              \
+        cufftResult r_ = (call);                                                                      \
+        if (r_ != CUFFT_SUCCESS) {                                                                    \
+            set_err(ctx, MG_ERR_CUDA, "cuFFT error %d in %s at %s:%d", (int)r_, #call, __FILE__, __LINE__); \
+            throw CudaFail{MG_ERR_CUDA};                                                              \
+        }                                                                                             \
+    } while (0)
+
+static void pm_release_fft(PmWork &w)
+{
+    if (w.fwd) cufftDestroy(w.fwd);
+    if (w.inv) cufftDestroy(w.inv);
+    w.fwd = w.inv = 0;
+    for (double *p : {w.rho, w.phin, w.phi, w.table})
+        if (p) cudaFree(p);
+    if (w.spec) cudaFree(w.spec);
+    w.rho = w.phin = w.phi = w.table = nullptr;
+    w.spec = nullptr;
+    w.fft_n = 0;
+}
+
+static void pm_fft_setup(mg_ctx *ctx, int n)
+{
+    PmWork &w = pmw(ctx);
+    if (w.fft_n == n) return;
+    MG_CK(cudaStreamSynchronize(ctx->stream));
+    pm_release_fft(w);
+    const size_t cells = (size_t)n * n * n, modes = (size_t)n * n * (n / 2 + 1);
+    MG_CK(cudaMalloc(&w.rho, sizeof(double) * cells));
+    MG_CK(cudaMalloc(&w.phin, sizeof(double) * cells));
+    MG_CK(cudaMalloc(&w.phi, sizeof(double) * cells));
+    MG_CK(cudaMalloc(&w.table, sizeof(double) * n));
+    MG_CK(cudaMalloc(&w.spec, sizeof(cufftDoubleComplex) * modes));
+    MG_CUFFT(cufftPlan3d(&w.fwd, n, n, n, CUFFT_D2Z));
+    MG_CUFFT(cufftPlan3d(&w.inv, n, n, n, CUFFT_Z2D));
+    MG_CUFFT(cufftSetStream(w.fwd, ctx->stream));
+    MG_CUFFT(cufftSetStream(w.inv, ctx->stream));
+    k_lap_table<<<(n + 127) / 128, 128, 0, ctx->stream>>>(w.table, n);
+    MG_CK(cudaGetLastError());
+    MG_CK(cudaMemsetAsync(w.phi, 0, sizeof(double) * cells, ctx->stream));
+    w.fft_n = n;
+}
+
+// Lap Phi = (3/2) Omega_m a^-1 delta (Eq. GR_poisson_codeunit), solved with
+// the 7-point Green's function by FFT (Sec. 3.1); the zero mode is dropped.
+static void newton_potential_dev(mg_ctx *ctx, int n, double a, double om, const double *delta, double *out)
+{
+    PmWork &w = pmw(ctx);
+    const double scale = 1.5 * om / a / ((double)n * n * n);
+    MG_CUFFT(cufftExecD2Z(w.fwd, const_cast<double *>(delta), w.spec));
+    const long long modes = (long long)n * n * (n / 2 + 1);
+    k_green<<<grid1(modes), 256, 0, ctx->stream>>>(w.spec, n, w.table, scale);
+    MG_CK(cudaGetLastError());
+    MG_CUFFT(cufftExecZ2D(w.inv, w.spec, out));
+}
+
+static double E_lcdm(double a, double om) { return std::sqrt(om * std::pow(a, -3.0) + (1.0 - om)); }
 
 // deposit on device pointers
 void cic_deposit_dev(mg_ctx *ctx, int ng, const float *pos, long long np, double *delta)
@@ -122,6 +273,7 @@ void mg_pm_free(mg_ctx *ctx)
 {
     if (!ctx || !ctx->pm) return;
     if (ctx->pm->acc) cudaFree(ctx->pm->acc);
+    pm_release_fft(*ctx->pm);
     delete ctx->pm;
     ctx->pm = nullptr;
 }
@@ -164,12 +316,89 @@ int pm_cic_index(mg_ctx *ctx, int ng, const float *pos, long long np, int *idx_o
     return MG_OK;
 }
 
+int pm_newton_potential(mg_ctx *ctx, int ng, double a, double omega_m, const double *delta, double *phi_out)
+{
+    if (!ctx) return MG_ERR_ARG;
+    if (!delta || !phi_out || ng < 2 || ng % 2 || !(a > 0))
+        return set_err(ctx, MG_ERR_ARG, "bad pm_newton_potential arguments");
+    try {
+        enter(ctx);
+        const size_t b = sizeof(double) * (size_t)ng * ng * ng;
+        const double *dd = (const double *)stage_in(ctx, 0, delta, b, true);
+        double *dp = (double *)stage_in(ctx, 1, phi_out, b, false);
+        pm_fft_setup(ctx, ng);
+        newton_potential_dev(ctx, ng, a, omega_m, dd, dp);
+        stage_out(ctx, phi_out, dp, b);
+        MG_CK(cudaStreamSynchronize(ctx->stream));
+        leave(ctx);
+    } catch (CudaFail &f) {
+        return f.code;
+    }
+    return MG_OK;
+}
+
 int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats)
 {
-    (void)st;
-    (void)opts;
-    (void)stats;
-    return set_err(ctx, MG_ERR_ARG, "pm_step: not available in this build");
+    if (!ctx) return MG_ERR_ARG;
+    if (!st || !st->pos || !st->mom || st->np < 1) return set_err(ctx, MG_ERR_ARG, "bad pm_state");
+    if (st->model != 0 && st->model != 1) return set_err(ctx, MG_ERR_ARG, "model must be 0 (GR) or 1 (nDGP)");
+    if (st->model == 1 ? !valid_ng(st->ng) : (st->ng < 2 || st->ng % 2))
+        return set_err(ctx, MG_ERR_ARG, "ng = %d not supported", st->ng);
+    if (!(st->a > 0) || !(st->da > 0) || !(st->omega_m > 0) || (st->model == 1 && !(st->dgp.rc_h0 > 0)))
+        return set_err(ctx, MG_ERR_ARG, "a, da, omega_m (and rc_h0) must be > 0");
+    mg_opts o;
+    if (opts)
+        o = *opts;
+    else
+        mg_opts_default(&o);
+    int rc = check_opts(ctx, o);
+    if (rc) return rc;
+    mg_stats loc{};
+    try {
+        enter(ctx);
+        const int n = st->ng;
+        const size_t pb = sizeof(float) * 3 * (size_t)st->np, cb = sizeof(double) * (size_t)n * n * n;
+        float *dpos = (float *)stage_in(ctx, 0, st->pos, pb, true);
+        float *dmom = (float *)stage_in(ctx, 1, st->mom, pb, true);
+        pm_fft_setup(ctx, n);
+        PmWork &w = pmw(ctx);
+        cic_deposit_dev(ctx, n, dpos, st->np, w.rho);
+        newton_potential_dev(ctx, n, st->a, st->omega_m, w.rho, w.phin);
+        const double *dphi = nullptr;
+        if (st->model == 1) {
+            double *phib = w.phi;
+            if (st->phi_ws) {
+                phib = (double *)stage_in(ctx, 2, st->phi_ws, cb, true);
+                o.warm_start = 1;
+            } else {
+                o.warm_start = 0;
+            }
+            rc = solve_dgp_dev(ctx, n, st->a, st->omega_m, st->dgp.rc_h0, w.rho, phib, o, &loc);
+            if (rc < 0) {
+                leave(ctx);
+                if (stats) *stats = loc;
+                return rc;
+            }
+            dphi = phib;
+            if (st->phi_ws) stage_out(ctx, st->phi_ws, phib, cb);
+        }
+        const double a = st->a, da = st->da, om = st->omega_m;
+        const double dak = st->first ? 0.5 * da : da;
+        const double ck = dak / (a * E_lcdm(a, om));
+        const double am = a + 0.5 * da;
+        const double cd = da / (std::pow(am, 3.0) * E_lcdm(am, om));
+        k_kick_drift<<<grid1(st->np), 256, 0, ctx->stream>>>(dpos, dmom, st->np, n, w.phin, dphi, ck, cd);
+        MG_CK(cudaGetLastError());
+        stage_out(ctx, st->pos, dpos, pb);
+        stage_out(ctx, st->mom, dmom, pb);
+        st->a += da;
+        st->first = 0;
+        leave(ctx);
+    } catch (CudaFail &f) {
+        return f.code;
+    }
+    if (stats) *stats = loc;
+    return rc;
 }
 
 int mg_solve_adjoint(mg_ctx *ctx, const mg_grid *g, const mg_dgp_params *p, const mg_opts *opts, const double *phi,

@@ -111,23 +111,18 @@ static void free_pyramid(Pyramid<T> *P)
 }
 
 template <typename T>
-static std::map<int, Pyramid<T> *> &pyr_map(mg_ctx *ctx);
+static std::map<int, Pyramid<T> *> &pyr_map(mg_ctx *ctx, bool corr);
 template <>
-std::map<int, Pyramid<double> *> &pyr_map<double>(mg_ctx *ctx) { return ctx->p64; }
+std::map<int, Pyramid<double> *> &pyr_map<double>(mg_ctx *ctx, bool corr) { return corr ? ctx->p64c : ctx->p64; }
 template <>
-std::map<int, Pyramid<float> *> &pyr_map<float>(mg_ctx *ctx) { return ctx->p32; }
+std::map<int, Pyramid<float> *> &pyr_map<float>(mg_ctx *ctx, bool corr) { return corr ? ctx->p32c : ctx->p32; }
 
 template <typename T>
 Pyramid<T> *get_pyramid(mg_ctx *ctx, int n, bool correction)
 {
-    auto &mp = pyr_map<T>(ctx);
+    auto &mp = pyr_map<T>(ctx, correction);
     auto it = mp.find(n);
-    if (it != mp.end()) {
-        if (!correction || it->second->correction) return it->second;
-        MG_CK(cudaStreamSynchronize(ctx->stream));
-        free_pyramid(it->second);
-        mp.erase(it);
-    }
+    if (it != mp.end()) return it->second;
     auto *P = new Pyramid<T>();
     P->n0 = n;
     P->nlev = (int)level_count(n);
@@ -188,7 +183,7 @@ Pyramid<T> *get_pyramid(mg_ctx *ctx, int n, bool correction)
         for (int c = 0; c < 2; ++c) L.fbuf[c] = take();
         for (int c = 0; c < 2; ++c) L.ur[c] = take();
         for (int c = 0; c < 2; ++c) L.base[c] = correction ? take() : nullptr;
-        for (int c = 0; c < 2; ++c) L.f[c] = (l == 0) ? nullptr : L.fbuf[c];
+        for (int c = 0; c < 2; ++c) L.f[c] = (l == 0 && !correction) ? nullptr : L.fbuf[c];
         L.sc = P->scal + l;
     }
     P->bytes = total + small;
@@ -212,6 +207,14 @@ static void smooth_half(mg_ctx *ctx, Pyramid<T> &P, int l, int colour)
     cudaStream_t st = ctx->stream;
     LevArrays<T> &L = P.L[l];
     const bool prof = ctx->prof_on && l == 0;
+    // inside a capture the events must become external event-record nodes
+    // (timestamps); outside a capture the external flag is not allowed
+    unsigned int flags = cudaEventRecordDefault;
+    if (prof) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        MG_CK(cudaStreamIsCapturing(st, &cs));
+        if (cs == cudaStreamCaptureStatusActive) flags = cudaEventRecordExternal;
+    }
     if (prof) {
         const size_t need = 2 * (size_t)(ctx->prof_k + 1);
         while (ctx->pev.size() < need) {
@@ -219,11 +222,11 @@ static void smooth_half(mg_ctx *ctx, Pyramid<T> &P, int l, int colour)
             MG_CK(cudaEventCreate(&e));
             ctx->pev.push_back(e);
         }
-        MG_CK(cudaEventRecord(ctx->pev[2 * ctx->prof_k], st));
+        MG_CK(cudaEventRecordWithFlags(ctx->pev[2 * ctx->prof_k], st, flags));
     }
     launch_smooth<T>(L, &L, P.opT, colour, st);
     if (prof) {
-        MG_CK(cudaEventRecord(ctx->pev[2 * ctx->prof_k + 1], st));
+        MG_CK(cudaEventRecordWithFlags(ctx->pev[2 * ctx->prof_k + 1], st, flags));
         ++ctx->prof_k;
     }
 }
@@ -426,14 +429,116 @@ static int solve_plain(mg_ctx *ctx, int n, const ModelDesc &md, const double *de
     return rc;
 }
 
+// Mixed precision (defect correction / iterative refinement): the FP64
+// master field u and the FP64 finest-level defect d = L(u) drive FP32 FAS
+// cycles on the correction e, which solve L(u + e) - L(u) = -d with the base
+// field b = fl32(u) frozen (operator N(b + e) - N(b) in cancellation-free
+// form, so the FP32 corrections keep their own relative precision); then
+// u += e and the defect is recomputed in FP64.  Norms, the compatibility
+// constants and the coarsest solve are FP64.
 int solve_mixed(mg_ctx *ctx, int n, const ModelDesc &md, const double *delta, double *phi, const mg_opts &o,
                 mg_stats *st)
 {
-    (void)n; (void)md; (void)delta; (void)phi; (void)o; (void)st;
-    return set_err(ctx, MG_ERR_ARG, "MG_PREC_MIXED: not available in this build");
+    Pyramid<double> &P64 = *get_pyramid<double>(ctx, n, false);
+    Pyramid<float> &P32 = *get_pyramid<float>(ctx, n, true);
+    cudaStream_t s = ctx->stream;
+    const long long cnt = (long long)n * n * n;
+    upload_op(ctx, P64, md);
+    upload_op(ctx, P32, md);
+    MG_CK(cudaMemsetAsync(P64.scal, 0, sizeof(LevScal) * P64.nlev, s));
+    MG_CK(cudaMemsetAsync(P32.scal, 0, sizeof(LevScal) * P32.nlev, s));
+    MG_CK(cudaEventRecord(ctx->t0, s));
+    LevScal *s0 = P64.scal;
+    LevArrays<double> &U64 = P64.L[0];
+    LevArrays<float> &E0 = P32.L[0];
+    // source prep in FP64, density pyramid in FP32
+    launch_mean_nat(delta, cnt, &s0->mean, P64.rb, s);
+    launch_split<double>(delta, n, U64.s, md.s_coef, &s0->mean, s);
+    launch_rms_nat(delta, cnt, md.eref_coef, &s0->mean, &s0->aux, P64.rb, s);
+    launch_convert<float, double>(E0.s, U64.s, U64.ncol, s);
+    for (int l = 0; l + 1 < P32.nlev; ++l) launch_restrict_plain<float>(P32.L[l].s, P32.L[l].n, P32.L[l + 1].s, s);
+    double *Uu[2] = {U64.U(0), U64.U(1)};
+    if (o.warm_start) {
+        launch_split<double>(phi, n, Uu, 1.0, nullptr, s);
+    } else {
+        MG_CK(cudaMemsetAsync(Uu[0], 0, sizeof(double) * U64.ncol, s));
+        MG_CK(cudaMemsetAsync(Uu[1], 0, sizeof(double) * U64.ncol, s));
+    }
+    float *D[2] = {E0.fbuf[0], E0.fbuf[1]};
+    launch_resid_norm<double>(U64, P64.opT, P64.rb, s, D);
+    LevScal h;
+    read_scal(ctx, s0, &h);
+    const double eps_ref = h.aux;
+    double eps = std::sqrt(std::fmax(h.eps2, 0.0));
+    mg_stats loc{};
+    loc.eps_ref = eps_ref;
+    loc.eps[0] = eps;
+    loc.n_eps = 1;
+    if (!std::isfinite(eps) || !std::isfinite(eps_ref)) {
+        if (st) *st = loc;
+        return set_err(ctx, MG_ERR_NONFINITE, "non-finite initial residual (delta has NaN/Inf?)");
+    }
+    const int inner = std::max(1, o.inner_cycles);
+    const long long per_cycle = cycle_updates(P32, o, 0, o.cycle);
+    const long long per_launch = cycle_launches(P32, o, 0, o.cycle) + 1;
+    long long launches = 6 + (P32.nlev - 1) + (o.warm_start ? 1 : 0);
+    int cyc = 0, outer = 0;
+    bool conv = eps <= o.rtol * eps_ref + o.atol;
+    while (!conv && cyc < o.max_cycles) {
+        // base field b = fl32(u) on every level, correction e = 0
+        launch_convert<float, double>(E0.base, Uu, U64.ncol, s);
+        for (int l = 0; l + 1 < P32.nlev; ++l)
+            launch_restrict_plain<float>(P32.L[l].base, P32.L[l].n, P32.L[l + 1].base, s);
+        launch_set_corr_scalars(P32.scal, s0, P32.nlev, s);
+        MG_CK(cudaMemsetAsync(E0.U(0), 0, sizeof(float) * E0.ncol, s));
+        MG_CK(cudaMemsetAsync(E0.U(1), 0, sizeof(float) * E0.ncol, s));
+        for (int k = 0; k < inner && cyc < o.max_cycles; ++k) {
+            cycle_and_norm(ctx, P32, o);
+            ++cyc;
+            launches += per_launch;
+            if (ctx->prof_on) {
+                MG_CK(cudaStreamSynchronize(s));
+                loc.fine_smooth_ms += prof_collect(ctx);
+                loc.fine_smooth_launches += ctx->prof_k;
+            }
+        }
+        float *Ee[2] = {E0.U(0), E0.U(1)};
+        launch_add_correction(Uu, Ee, U64.ncol, s);
+        launch_resid_norm<double>(U64, P64.opT, P64.rb, s, D);
+        launches += 3 + (P32.nlev - 1) + 1;
+        ++outer;
+        read_scal(ctx, s0, &h);
+        eps = std::sqrt(std::fmax(h.eps2, 0.0));
+        if (loc.n_eps < 65) loc.eps[loc.n_eps++] = eps;
+        if (!std::isfinite(eps)) {
+            loc.cycles = cyc;
+            if (st) *st = loc;
+            return set_err(ctx, MG_ERR_NONFINITE, "non-finite residual after correction %d", outer);
+        }
+        conv = eps <= o.rtol * eps_ref + o.atol;
+    }
+    const double c_final = h.c, clamps = h.clamps;
+    launch_mean_split<double>(Uu, U64.ncol, &s0->mean, P64.rb, s);
+    launch_merge<double>(Uu, n, phi, &s0->mean, s);
+    MG_CK(cudaEventRecord(ctx->t1, s));
+    read_scal(ctx, s0, &h);
+    float ms = 0.f;
+    MG_CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
+    loc.cycles = cyc;
+    loc.c_final = c_final;
+    loc.mean_shift = h.mean;
+    loc.sqrt_clamps = (long long)clamps;
+    loc.ms = ms;
+    loc.cell_updates = per_cycle * cyc;
+    loc.kernel_launches = launches;
+    const int rc = conv ? MG_OK : MG_WARN_NOT_CONVERGED;
+    loc.status = rc;
+    if (st) *st = loc;
+    if (!conv) set_err(ctx, rc, "not converged after %d FP32 cycles: eps/eps_ref = %g", cyc, eps / eps_ref);
+    return rc;
 }
 
-static int check_opts(mg_ctx *ctx, const mg_opts &o)
+int check_opts(mg_ctx *ctx, const mg_opts &o)
 {
     if (o.pre < 0 || o.post < 0 || o.pre + o.post == 0 || o.max_cycles < 0 || o.max_cycles > 64)
         return set_err(ctx, MG_ERR_ARG, "bad pre/post/max_cycles");
@@ -465,6 +570,17 @@ static int solve_any(mg_ctx *ctx, int n, const ModelDesc &md, const double *delt
         rc = solve_mixed(ctx, n, md, delta, phi, o, st);
     if (rc >= 0) stage_out(ctx, phi_io, phi, bytes);
     return rc;
+}
+
+// nDGP solve on device arrays (used by the particle-mesh step)
+int solve_dgp_dev(mg_ctx *ctx, int n, double a, double om, double rc, const double *delta, double *phi,
+                  const mg_opts &o, mg_stats *st)
+{
+    const double beta = beta_dgp(a, om, rc);
+    const double alpha = 3.0 * beta * a * a / (rc * rc);
+    ModelDesc md{0, alpha, 0, 0.0, 0.0, (alpha / beta) * om / a, om / (a * beta)};
+    if (o.precision == MG_PREC_FP64) return solve_plain<double>(ctx, n, md, delta, phi, o, st);
+    return solve_mixed(ctx, n, md, delta, phi, o, st);
 }
 
 }  // namespace mg
@@ -532,8 +648,10 @@ void mg_ctx_destroy(mg_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->p64) free_pyramid(p.second);
     for (auto &p : ctx->p32) free_pyramid(p.second);
+    for (auto &p : ctx->p64c) free_pyramid(p.second);
+    for (auto &p : ctx->p32c) free_pyramid(p.second);
     mg_pm_free(ctx);
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < mg_ctx::NSTAGE; ++q)
         if (ctx->stage[q]) cudaFree(ctx->stage[q]);
     for (auto e : ctx->pev) cudaEventDestroy(e);
     if (ctx->hpin) cudaFreeHost(ctx->hpin);
@@ -565,7 +683,9 @@ long long mg_ctx_workspace_bytes(const mg_ctx *ctx)
     long long b = 0;
     for (auto &p : ctx->p64) b += (long long)p.second->bytes;
     for (auto &p : ctx->p32) b += (long long)p.second->bytes;
-    for (int q = 0; q < 4; ++q) b += (long long)ctx->stage_bytes[q];
+    for (auto &p : ctx->p64c) b += (long long)p.second->bytes;
+    for (auto &p : ctx->p32c) b += (long long)p.second->bytes;
+    for (int q = 0; q < mg_ctx::NSTAGE; ++q) b += (long long)ctx->stage_bytes[q];
     return b;
 }
 
@@ -674,6 +794,39 @@ static int op_smooth_t(mg_ctx *ctx, const mg_op_params *op, int n, double h, con
     launch_smooth<T>(L, &L, P.opT, colour, st);
     T *o2[2] = {L.U(0), L.U(1)};
     launch_merge<T>(o2, n, u_out, nullptr, st);
+    MG_CK(cudaStreamSynchronize(st));
+    return MG_OK;
+}
+
+// FP32 correction-form half-sweep (the inner smoother of MG_PREC_MIXED)
+static int op_smooth_corr_t(mg_ctx *ctx, const mg_op_params *op, int n, double h, const double *e_in,
+                            const double *base, const double *s, const double *f, double c, int colour,
+                            double *e_out)
+{
+    Pyramid<float> &P = *get_pyramid<float>(ctx, n, true);
+    ModelDesc md{op->model, op->alpha, op->nkmo, op->gamma, op->bterm, 1.0, 1.0};
+    upload_op(ctx, P, md);
+    cudaStream_t st = ctx->stream;
+    LevArrays<float> L = P.L[0];
+    L.h = h;
+    float *u[2] = {L.U(0), L.U(1)};
+    launch_split<float>(e_in, n, u, 1.0, nullptr, st);
+    launch_split<float>(base, n, L.base, 1.0, nullptr, st);
+    launch_split<float>(s, n, L.s, 1.0, nullptr, st);
+    if (f) {
+        launch_split<float>(f, n, L.fbuf, 1.0, nullptr, st);
+        L.f[0] = L.fbuf[0];
+        L.f[1] = L.fbuf[1];
+    } else {
+        L.f[0] = L.f[1] = nullptr;
+    }
+    LevScal hs{};
+    hs.c = c;
+    memcpy(ctx->hpin, &hs, sizeof hs);
+    MG_CK(cudaMemcpyAsync(L.sc, ctx->hpin, sizeof hs, cudaMemcpyHostToDevice, st));
+    launch_smooth<float>(L, &L, P.opT, colour, st);
+    float *o2[2] = {L.U(0), L.U(1)};
+    launch_merge<float>(o2, n, e_out, nullptr, st);
     MG_CK(cudaStreamSynchronize(st));
     return MG_OK;
 }
@@ -796,6 +949,28 @@ int mg_op_smooth(mg_ctx *ctx, const mg_op_params *op, int precision, int n, doub
         leave(ctx);
     } catch (CudaFail &f) {
         return f.code;
+    }
+    return rc;
+}
+
+int mg_op_smooth_corr(mg_ctx *ctx, const mg_op_params *op, int n, double h, const double *e_in, const double *base,
+                      const double *s, const double *f, double c, int colour, double *e_out)
+{
+    int rc = op_entry(ctx, n, {op, e_in, base, s, e_out}, 1);
+    if (rc) return rc;
+    const size_t b = sizeof(double) * (size_t)n * n * n;
+    try {
+        enter(ctx);
+        const double *de = (const double *)stage_in(ctx, 0, e_in, b, true);
+        const double *dbs = (const double *)stage_in(ctx, 1, base, b, true);
+        const double *ds = (const double *)stage_in(ctx, 2, s, b, true);
+        double *dout = (double *)stage_in(ctx, 3, e_out, b, false);
+        const double *df = (const double *)stage_in(ctx, 4, f, b, true);
+        rc = op_smooth_corr_t(ctx, op, n, h, de, dbs, ds, df, c, colour & 1, dout);
+        stage_out(ctx, e_out, dout, b);
+        leave(ctx);
+    } catch (CudaFail &fl) {
+        return fl.code;
     }
     return rc;
 }

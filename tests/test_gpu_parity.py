@@ -230,6 +230,21 @@ def test_device_and_host_pointers_agree_and_are_deterministic(B, ctx):
     assert np.array_equal(p.cpu().numpy(), phi_h)
 
 
+@pytest.mark.parametrize("graph", [1, 0])
+def test_profiling_events(B, ctx, graph):
+    """With profiling on, every finest-level half-sweep is bracketed by
+    events (graph nodes when captured): 2 (pre + post) launches per cycle."""
+    delta = config1_delta()
+    ctx.set_profiling(True)
+    try:
+        _, _, st = dgp_gpu(B, ctx, delta, 1.0, 0.3, 1.0, use_graph=graph)
+    finally:
+        ctx.set_profiling(False)
+    assert st.fine_smooth_launches == st.cycles * 2 * (2 + 2)
+    assert 0.0 < st.fine_smooth_ms < st.ms
+    assert st.kernel_launches > st.fine_smooth_launches
+
+
 def test_errors(B, ctx):
     z = np.zeros((20,) * 3)
     with pytest.raises(B.MGError) as e:

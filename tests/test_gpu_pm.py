@@ -1,0 +1,74 @@
+"""GPU parity of the particle-mesh rows: the FFT Newtonian potential, the
+leapfrog step with the nDGP field solved every step, and conservation of
+total momentum by the GPU forces.  Positions and momenta are FP32 state:
+they must agree with the oracle's step to within a few FP32 ulps."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_00566_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from test_gpu_parity import B, ctx  # noqa: E402,F401
+
+
+def test_newton_potential(B, ctx):
+    n = 24
+    delta = inputs.white_noise(n, 70)
+    ref = oracle.newton_potential(delta, 0.5, 0.3)
+    out = np.empty_like(delta)
+    B.pm_newton_potential(ctx, n, 0.5, 0.3, delta, out)
+    assert np.abs(out - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def _load(ng, nps, seed, a):
+    om = 0.3
+    D = inputs.growth_lcdm(a, om)
+    f = inputs.growth_rate_lcdm(a, om)
+    vel = a * a * oracle.E_lcdm(a, om) * f
+    pk = inputs.pk_cutoff()
+    return inputs.zeldovich(nps, ng, 2.0 * ng, pk, D, seed=seed, vel_factor=vel * D)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_pm_steps_match_oracle(B, ctx, model):
+    """Five leapfrog steps from a = 0.1 (the first a half kick), GR and
+    nDGP (H0 r_c = 1), 16^3 particles on a 32^3 mesh."""
+    ng, nps, a0, da = 32, 16, 0.1, 0.05
+    pos, mom = _load(ng, nps, 7, a0)
+    p_ref, m_ref = pos.copy(), mom.copy()
+    p_gpu, m_gpu = pos.copy(), mom.copy()
+    phi_ref = None
+    phi_ws = np.zeros((ng,) * 3)
+    st = B.make_pm_state(p_gpu, m_gpu, ng, 2.0 * ng, 0.3, a0, da, model=model, rc_h0=1.0, first=True,
+                         phi_ws=phi_ws if model else None)
+    a = a0
+    o = B.opts(rtol=1e-12, max_cycles=40)
+    for s in range(5):
+        p_ref, m_ref, phi_ref = oracle.pm_step(p_ref, m_ref, ng, nps, 0.3, a, da, model, 1.0, first=(s == 0),
+                                               phi_guess=phi_ref, opts=oracle.Opts(rtol=1e-12, max_cycles=40))
+        B.pm_step(ctx, st, o)
+        a += da
+    assert st.a == pytest.approx(a) and st.first == 0
+    ulp = np.spacing(np.float32(ng))
+    dp = np.abs(p_gpu.astype(np.float64) - p_ref.astype(np.float64))
+    dp = np.minimum(dp, ng - dp)                        # periodic seam
+    assert dp.max() <= 4 * ulp, dp.max()
+    assert np.abs(m_gpu - m_ref).max() <= 1e-5 * np.abs(m_ref).max()
+    if model:
+        assert np.abs(phi_ws - phi_ref).max() < 1e-8 * np.abs(phi_ref).max()
+
+
+def test_pm_momentum_conserved(B, ctx):
+    """One kick from rest: sum of the momentum changes is zero to FP32
+    rounding of the individual kicks (CIC + symmetric Green's function +
+    antisymmetric gradient)."""
+    ng, nps = 32, 16
+    pos, _ = _load(ng, nps, 9, 1.0)
+    mom = np.zeros_like(pos)
+    st = B.make_pm_state(pos, mom, ng, 64.0, 0.3, 1.0, 0.01, model=0, first=False)
+    B.pm_step(ctx, st, B.opts())
+    tot = mom.astype(np.float64).sum(axis=0)
+    assert np.abs(tot).max() < 1e-5 * np.abs(mom).sum()
