@@ -199,6 +199,33 @@ int mg_solve_kmouflage(mg_ctx *ctx, const mg_grid *g, const mg_kmo_params *p,
 int pm_cic_deposit(mg_ctx *ctx, int ng, const float *pos, long long np,
                    double *delta_out);
 
+/*
+ * pm_cic_deposit for callers that cannot allocate device memory: code
+ * running while a CUDA graph is captured (allocation is illegal there),
+ * applications whose device memory all belongs to their own pool, and
+ * pipelines that cannot afford the device synchronisation of cudaMalloc.
+ * The paper has no counterpart; this is a deployment variant of the CIC
+ * deposit above with the same result (same kernels, same fixed-point sums).
+ *  - Allocates nothing: no mg_ctx, no cudaMalloc/cudaFree, no allocating
+ *    library call.  Its scratch (fixed-point accumulator, reduction
+ *    partials, mean, counter) is one static device array of 16 MiB + 8 KiB
+ *    + 256 B that every GPU loading the library holds until process exit.
+ *  - ng <= 128 (the array holds 128^3 cells): larger ng returns MG_ERR_ARG,
+ *    as do ng < 2, np < 1, NULL or host pointers.  pos (np x 3 FP32 in
+ *    [0, ng)) and delta_out (ng^3 FP64) must be device arrays of the
+ *    current device; work is queued on cuda_stream (a cudaStream_t, NULL =
+ *    legacy default stream) and the call returns without synchronising.
+ *  - The first call on a device (the current one) looks up the array's
+ *    device address with cudaGetSymbolAddress; make that first call before
+ *    any stream capture.
+ *  - Every call shares the one array, which keeps the last call's contents
+ *    (each call clears what must start at zero): calls whose work overlaps
+ *    on the GPU (other streams, other threads) race and corrupt each other.
+ * Returns MG_OK, MG_ERR_ARG or MG_ERR_CUDA.
+ */
+int pm_cic_deposit_noalloc(int ng, const float *pos, long long np,
+                           double *delta_out, void *cuda_stream);
+
 /* Lower CIC cell per axis, floor(x - 1/2) mod ng, as used by
  * pm_cic_deposit (np x 3 int32 output); for checking the indexing. */
 int pm_cic_index(mg_ctx *ctx, int ng, const float *pos, long long np,

@@ -92,6 +92,7 @@ def _declare(L):
                                          _P(mg_stats)]),
         "pm_cic_deposit": (C.c_int, [_VP, C.c_int, _VP, C.c_longlong, _VP]),
         "pm_cic_index": (C.c_int, [_VP, C.c_int, _VP, C.c_longlong, _VP]),
+        "pm_cic_deposit_noalloc": (C.c_int, [C.c_int, _VP, C.c_longlong, _VP, _VP]),
         "pm_step": (C.c_int, [_VP, _P(pm_state), _P(mg_opts), _P(mg_stats)]),
         "pm_newton_potential": (C.c_int, [_VP, C.c_int, C.c_double, C.c_double, _VP, _VP]),
         "mg_solve_adjoint": (C.c_int, [_VP, _P(mg_grid), _P(mg_dgp_params), _P(mg_opts), _VP, _VP, _VP, _VP,

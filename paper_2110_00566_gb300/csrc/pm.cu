@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include <cufft.h>
 
@@ -411,4 +412,95 @@ int mg_solve_adjoint(mg_ctx *ctx, const mg_grid *g, const mg_dgp_params *p, cons
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// CIC deposit for callers that cannot allocate device memory
+//
+// pm_cic_deposit keeps its fixed-point accumulator and reduction partials in
+// memory it allocates on first use.  Some callers cannot let a library call
+// cudaMalloc: code that runs while a CUDA graph is being captured (an
+// allocation there is illegal), applications that hand all device memory to
+// their own pool up front, and real-time pipelines in which cudaMalloc's
+// implicit device synchronisation is not acceptable.  This variant runs the
+// same kernels with all of its scratch in one file-scope device array whose
+// size is fixed when the library is loaded: the accumulator for meshes up
+// to NOALLOC_MAX_NG^3 cells, the reduction partials, the mean and the
+// arrival counter (16 MiB + 8 KiB + 256 B on every GPU that loads the
+// library, held until the process exits).
+// ---------------------------------------------------------------------------
+namespace mg {
+
+constexpr int NOALLOC_MAX_NG = 128;
+constexpr long long NOALLOC_CELLS = (long long)NOALLOC_MAX_NG * NOALLOC_MAX_NG * NOALLOC_MAX_NG;
+constexpr int NOALLOC_BLOCKS = MAX_RED_BLOCKS / 4;   // the mean reduction's largest grid
+constexpr size_t NOALLOC_BYTES = sizeof(unsigned long long) * (size_t)NOALLOC_CELLS +
+                                 sizeof(double) * (size_t)NOALLOC_BLOCKS + 256;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+static void *g_noalloc_addr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
+
+// device address of the scratch array on the current device, looked up once
+// per device (host code only holds a stand-in for the array's name)
+static int noalloc_scratch(void **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return MG_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return MG_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return MG_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return MG_OK;
+}
+
+// the accumulator must start at zero for every call, and so must the arrival
+// counter of the reduction (it is also reset by the last block of each use)
+__global__ void __launch_bounds__(256)
+k_noalloc_clear(unsigned long long *__restrict__ acc, long long cnt, unsigned int *counter)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) acc[q] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0u;
+}
+
+}  // namespace mg
+
+extern "C" int pm_cic_deposit_noalloc(int ng, const float *pos, long long np, double *delta_out, void *cuda_stream)
+{
+    using namespace mg;
+    if (!pos || !delta_out || np < 1 || ng < 2) return MG_ERR_ARG;
+    if (ng > NOALLOC_MAX_NG) return MG_ERR_ARG;      // the scratch holds NOALLOC_MAX_NG^3 cells
+    if (!is_device_ptr(pos) || !is_device_ptr(delta_out)) return MG_ERR_ARG;
+    void *base = nullptr;
+    const int rc = noalloc_scratch(&base);
+    if (rc != MG_OK) return rc;
+    unsigned char *b = (unsigned char *)base;
+    unsigned long long *acc = (unsigned long long *)b;
+    double *partials = (double *)(b + sizeof(unsigned long long) * (size_t)NOALLOC_CELLS);
+    double *mean = partials + NOALLOC_BLOCKS;
+    unsigned int *counter = (unsigned int *)(mean + 1);
+    const cudaStream_t st = (cudaStream_t)cuda_stream;
+    const long long cnt = (long long)ng * ng * ng;
+    k_noalloc_clear<<<grid1(cnt), 256, 0, st>>>(acc, cnt, counter);
+    k_cic_deposit<<<grid1(np), 256, 0, st>>>(pos, np, ng, acc);
+    k_cic_finish<<<grid1(cnt), 256, 0, st>>>(acc, cnt, (double)cnt / (double)np, delta_out);
+    RedBuf rb{partials, counter, NOALLOC_BLOCKS};
+    launch_mean_nat(delta_out, cnt, mean, rb, st);
+    k_sub_mean<<<grid1(cnt), 256, 0, st>>>(delta_out, cnt, mean);
+    if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
+    return MG_OK;
+}
 
