@@ -10,6 +10,11 @@ solve from phi = 0 to eps/eps_ref < 1e-8 with V(2,2) cycles (source prep,
 all cycles, gauge fix), inputs resident in HBM.  The metric is smoother
 cell-updates (summed over all levels and cycles) per second.
 
+`value` is the FP64 solve (every level FP64, the paper's precision).  The
+same line reports the mixed-precision form (FP32 correction cycles, FP64
+defect) under "forms", timed the same way, with its speedup and its phi
+difference from the FP64 solution.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
   python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
 
@@ -30,6 +35,11 @@ sys.path.insert(0, ROOT)
 METRIC = "nDGP MG-solve Gcell-updates/s @512^3"
 UNIT = "Gcell-updates/s"
 HBM_PEAK_FALLBACK = 6800.0
+# algorithmic FP64 operations per cell of the nDGP half-sweep (sqrt counted
+# once, an FMA as two): S_a, their differences and C_ab (3 + 3 + 9 adds),
+# the two sums of squares (2 x 5), Q (3), Sigma (1), the sqrt argument (2),
+# sqrt (1), N (2), the face sum (2), N + f - c (2), the update (3) = 41
+FLOPS_PER_CELL_FP64 = 41
 
 
 def args():
@@ -46,6 +56,7 @@ def args():
     p.add_argument("--rtol", type=float, default=1e-8)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-forms", action="store_true")
     return p.parse_args()
 
 
@@ -119,7 +130,6 @@ def cpu_baseline(delta_host, a, sample_cycles=1):
     dt = time.perf_counter() - t
     ng = a.ng
     per_cycle = 0
-    n = ng
     levels = oracle.num_levels(ng)
     for l in range(levels):
         cells = (ng >> l) ** 3
@@ -131,6 +141,12 @@ def cpu_baseline(delta_host, a, sample_cycles=1):
             "seconds": dt}
 
 
+def workload_name(a):
+    return ("nDGP FAS V(2,2) solve to eps/eps_ref<%g, %d^3 mesh, CIC of %d^3 Zel'dovich particles "
+            "(P~k^0.96 e^-k/5, sigma8=0.8, z=0), L=%g Mpc/h, a=1, Omega_m=0.3, H0 rc=%g"
+            % (a.rtol, a.ng, a.np, a.box, a.rc))
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return
@@ -139,8 +155,6 @@ def run_reference(a, rank, world):
     pos = particles(a, 0)
     delta, _ = oracle.cic_deposit(pos, a.ng, a.np)
     vals = []
-    for _ in range(a.warmup):
-        pass                                    # the oracle has no warm-up state
     t0 = time.perf_counter()
     for _ in range(a.steps):
         cb = cpu_baseline(delta, a)
@@ -151,9 +165,7 @@ def run_reference(a, rank, world):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "nDGP FAS V(2,2) solve, %d^3 mesh, CIC of %d^3 Zel'dovich particles, L=%g Mpc/h, "
-                                   "a=1, Omega_m=0.3, H0 rc=%g" % (a.ng, a.np, a.box, a.rc),
-                       "sample": cb["sample"]},
+            "config": {"workload": workload_name(a), "sample": cb["sample"]},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -165,12 +177,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
-        import __graft_entry__
         from oracle import build as ob
         ob.build()
         return run_reference(a, rank, world)
 
-    import numpy as np
     import torch
     dist = None
     if world > 1:
@@ -191,128 +201,137 @@ def main():
     pos = torch.from_numpy(particles(a, rank)).to(dev)
     delta = torch.empty((ng, ng, ng), dtype=torch.float64, device=dev)
     B.pm_cic_deposit(ctx, ng, pos, delta)
-    phi = torch.zeros_like(delta)
-    prec = B.MG_PREC_FP64 if a.precision == "fp64" else B.MG_PREC_MIXED
-    o = B.opts(rtol=a.rtol, precision=prec)
-    inst = dict(ng=ng, box_mpch=a.box, a=1.0, omega_m=0.3, rc_h0=a.rc, delta=delta, phi=phi)
+    hbm_peak, peak_src = peaks()
 
-    for _ in range(a.warmup):
-        B.mg_solve_dgp(ctx, [inst], o)
-    torch.cuda.synchronize(dev)
-
-    ctx.set_profiling(True)
-    clocks = Clocks(local)
-    clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    stats = []
-    for _ in range(a.steps):
-        rcode, st = B.mg_solve_dgp(ctx, [inst], o)
-        stats.append(st[0])
-    e1.record()
-    torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
-    ck = clocks.stop()
-    ctx.set_profiling(False)
-    ms = e0.elapsed_time(e1)
-    updates = sum(s.cell_updates for s in stats)
-    launches = sum(s.kernel_launches for s in stats)
-    fs_ms = sum(s.fine_smooth_ms for s in stats)
-    fs_n = sum(s.fine_smooth_launches for s in stats)
-    t = torch.tensor([ms, float(updates)], dtype=torch.float64, device=dev)
-    if dist:
-        mx = t.clone()
+    def reduce_max_sum(x, y):
+        t = torch.tensor([x, float(y)], dtype=torch.float64, device=dev)
+        if not dist:
+            return x, float(y)
+        mx, sm_ = t.clone(), t.clone()
         dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm_ = t.clone()
         dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
-        ms_max, upd_tot = float(mx[0]), float(sm_[1])
-    else:
-        ms_max, upd_tot = ms, float(updates)
-    value = upd_tot / (ms_max * 1e-3) / 1e9
+        return float(mx[0]), float(sm_[1])
 
-    # end to end through the same C-ABI call with host buffers (pinned):
-    # H2D of delta and D2H of phi inside the timed region
-    e2e = None
-    if not a.no_e2e:
+    def timed(precision):
+        """W untimed + K timed solves; CUDA events on the caller's stream
+        bracket the library's stream (ordered by events at entry/exit)."""
+        prec = B.MG_PREC_FP64 if precision == "fp64" else B.MG_PREC_MIXED
+        o = B.opts(rtol=a.rtol, precision=prec, max_cycles=60)
+        phi = torch.zeros_like(delta)
+        inst = dict(ng=ng, box_mpch=a.box, a=1.0, omega_m=0.3, rc_h0=a.rc, delta=delta, phi=phi)
+        for _ in range(a.warmup):
+            B.mg_solve_dgp(ctx, [inst], o)
+        torch.cuda.synchronize(dev)
+        ctx.set_profiling(True)
+        clocks = Clocks(local)
+        clocks.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        stats = []
+        for _ in range(a.steps):
+            _, st = B.mg_solve_dgp(ctx, [inst], o)
+            stats.append(st[0])
+        e1.record()
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        ck = clocks.stop()
+        ctx.set_profiling(False)
+        ms, upd = reduce_max_sum(e0.elapsed_time(e1), sum(s.cell_updates for s in stats))
+        r = {"value": upd / (ms * 1e-3) / 1e9, "ms_per_step": ms / a.steps, "clocks": ck, "stats": stats,
+             "phi": phi, "inst": inst, "o": o,
+             "launches": sum(s.kernel_launches for s in stats),
+             "avg_launch_ms": sum(s.fine_smooth_ms for s in stats) / max(1, sum(s.fine_smooth_launches for s in stats)),
+             "fine_launches": sum(s.fine_smooth_launches for s in stats)}
+        return r
+
+    def e2e(r):
+        """Same call with pinned host buffers: H2D of delta and D2H of phi
+        inside the timed region."""
         dh = delta.cpu().pin_memory()
         ph = torch.zeros_like(dh).pin_memory()
-        insth = dict(inst, delta=dh, phi=ph)
-        B.mg_solve_dgp(ctx, [insth], o)
+        insth = dict(r["inst"], delta=dh, phi=ph)
+        B.mg_solve_dgp(ctx, [insth], r["o"])
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
         upd = 0
         for _ in range(a.steps):
-            _, st = B.mg_solve_dgp(ctx, [insth], o)
+            _, st = B.mg_solve_dgp(ctx, [insth], r["o"])
             upd += st[0].cell_updates
-        dt = time.perf_counter() - t0
-        tt = torch.tensor([dt, float(upd)], dtype=torch.float64, device=dev)
-        if dist:
-            mx = tt.clone()
-            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-            sm_ = tt.clone()
-            dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
-            dt, upd = float(mx[0]), float(sm_[1])
-        e2e = {"value": upd / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * ng ** 3,
-               "d2h_bytes_per_step": 8 * ng ** 3}
+        dt, upd = reduce_max_sum(time.perf_counter() - t0, upd)
+        return {"value": upd / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * ng ** 3,
+                "d2h_bytes_per_step": 8 * ng ** 3}
+
+    def roofline(r, precision, fp64_tf):
+        ms = r["avg_launch_ms"]
+        if precision == "fp64":
+            # finest FP64 half-sweep: read both colours + the colour's s,
+            # write the colour = 2 s n^3 bytes (s = 8); FP64-pipe bound
+            alg = 2 * 8 * ng ** 3
+            gbs = alg / (ms * 1e-3) / 1e9
+            tf = FLOPS_PER_CELL_FP64 * (ng ** 3 / 2) / (ms * 1e-3) / 1e12
+            return {"bound": "alu", "achieved": tf, "peak": fp64_tf, "unit": "TFLOP/s", "frac": tf / fp64_tf,
+                    "traffic": None, "kernel": "k_smooth<double> finest half-sweep",
+                    "peak_source": "FP64 FMA rate measured by mg_probe_alu_peaks on this GPU",
+                    "alg_flops_per_cell": FLOPS_PER_CELL_FP64, "avg_launch_ms": ms, "launches": r["fine_launches"],
+                    "hbm_view": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                                 "alg_bytes_per_launch": alg, "peak_source": peak_src}}
+        # finest FP32 correction half-sweep: read e and the base field (both
+        # colours, 4 B each), s and f of the colour (2 B each), write the
+        # colour (2 B) = 14 n^3 bytes
+        alg = 14 * ng ** 3
+        gbs = alg / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": None, "kernel": "k_smooth<float, correction> finest half-sweep",
+                "peak_source": peak_src, "avg_launch_ms": ms, "launches": r["fine_launches"],
+                "alg_bytes_per_launch": alg}
+
+    primary = timed(a.precision)
+    second = None
+    if not a.no_forms:
+        second = timed("mixed" if a.precision == "fp64" else "fp64")
+    e2e_primary = None if a.no_e2e else e2e(primary)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    st0 = stats[-1]
-    hbm_peak, peak_src = peaks()
     fp64_tf, fp32_tf = ctx.probe_alu_peaks()
-    avg_launch_ms = fs_ms / max(fs_n, 1)
-    # dominant kernel: the finest-level half-sweep (K1).  Algorithmic bytes per
-    # launch: read both colour arrays, read the source of the updated colour,
-    # write the updated colour = 2 s ng^3 (s = 8 bytes FP64, 4 FP32).
-    s_bytes = 8 if a.precision == "fp64" else 4
-    alg_bytes = 2 * s_bytes * ng ** 3
-    achieved_gbs = alg_bytes / (avg_launch_ms * 1e-3) / 1e9
-    # algorithmic FP64 operations per cell of the nDGP half-sweep (sqrt and
-    # divide counted once each, an FMA as two)
-    flops_cell = 44
-    cells = ng ** 3 / 2
-    achieved_tf = flops_cell * cells / (avg_launch_ms * 1e-3) / 1e12
-    if a.precision == "fp64":
-        roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_tf, "unit": "TFLOP/s",
-                "frac": achieved_tf / fp64_tf, "traffic": None,
-                "kernel": "k_smooth<double> finest half-sweep",
-                "peak_source": "FP64 FMA rate measured by mg_probe_alu_peaks on this GPU",
-                "hbm_view": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": achieved_gbs / hbm_peak, "peak_source": peak_src},
-                "avg_launch_ms": avg_launch_ms, "launches": fs_n, "alg_bytes_per_launch": alg_bytes,
-                "alg_flops_per_cell": flops_cell}
-    else:
-        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": None, "kernel": "k_smooth<float> finest half-sweep",
-                "peak_source": peak_src, "avg_launch_ms": avg_launch_ms, "launches": fs_n,
-                "alg_bytes_per_launch": alg_bytes}
-    cb = None
-    if not a.no_cpu:
-        cb = cpu_baseline(delta.cpu().numpy(), a)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32+f64", "data": "synthetic",
-            "config": {"workload": "nDGP FAS V(2,2) solve to eps/eps_ref<%g, %d^3 mesh, CIC of %d^3 Zel'dovich "
-                                   "particles (P~k^0.96 e^-k/5, sigma8=0.8, z=0), L=%g Mpc/h, a=1, Omega_m=0.3, "
-                                   "H0 rc=%g" % (a.rtol, ng, a.np, a.box, a.rc),
-                       "precision": a.precision, "cycles_per_solve": st0.cycles,
+    st0 = primary["stats"][-1]
+    forms = {}
+    if second is not None:
+        name = "mixed" if a.precision == "fp64" else "fp64"
+        st1 = second["stats"][-1]
+        p0, p1 = primary["phi"], second["phi"]
+        l2 = float(torch.linalg.vector_norm(p1 - p0) / torch.linalg.vector_norm(p0))
+        forms[name] = {"value": second["value"], "unit": UNIT, "ms_per_step": second["ms_per_step"],
+                       "speedup_vs_primary": primary["ms_per_step"] / second["ms_per_step"],
+                       "phi_rel_l2_vs_primary": l2, "cycles_per_solve": st1.cycles,
+                       "final_eps_over_eps_ref": st1.eps[st1.n_eps - 1] / st1.eps_ref,
+                       "gpu_launches": second["launches"], "clocks": second["clocks"],
+                       "roofline": roofline(second, name, fp64_tf)}
+    cb = None if a.no_cpu else cpu_baseline(delta.cpu().numpy(), a)
+    line = {"metric": METRIC, "value": primary["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": primary["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(a), "precision": a.precision, "cycles_per_solve": st0.cycles,
                        "cell_updates_per_solve": st0.cell_updates,
+                       "final_eps_over_eps_ref": st0.eps[st0.n_eps - 1] / st0.eps_ref,
                        "l2": "inputs larger than L2 (delta %d MB, phi %d MB)" % (8 * ng ** 3 >> 20, 8 * ng ** 3 >> 20),
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
-            "gpu_launches": launches,
-            "clocks": ck,
-            "roofline": roof,
+            "gpu_launches": primary["launches"],
+            "clocks": primary["clocks"],
+            "roofline": roofline(primary, a.precision, fp64_tf),
             "alu_peaks_tflops": {"fp64": fp64_tf, "fp32": fp32_tf},
-            "e2e": e2e,
-            "cpu_baseline": cb}
+            "e2e": e2e_primary,
+            "cpu_baseline": cb,
+            "forms": forms}
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

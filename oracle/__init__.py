@@ -357,3 +357,44 @@ def pm_step(pos, mom, ng, np_side, omega_m, a, da, model=1, rc_h0=1.0, first=Fal
     am = a + 0.5 * da
     pos = (pos.astype(np.float64) + mom.astype(np.float64) * (da / (am ** 3 * E_lcdm(am, omega_m))))
     return _wrap32(pos, ng), mom, phi
+
+
+# ---------------------------------------------------------------------------
+# reference gradient of the nDGP solution map (brute force, small meshes)
+# ---------------------------------------------------------------------------
+
+def dgp_gradient(delta, a, omega_m, rc_h0, g, opts: Opts = None, step=1e-6):
+    """Gradient of L = <g, phi(delta, R_c)> for the discrete nDGP solve
+    (Sec. 3.2.3 operator with the compatibility projection, gauge <phi> = 0):
+    the dense Jacobians J = dF/dphi and B = dF/ddelta of the residual map
+    F(phi, delta) are taken by central differences of the oracle's own
+    residual at the converged phi, and J^T lambda = Pi g is solved with the
+    constant null direction pinned by adding 11^T/n^3 (J^T maps zero-mean
+    fields to zero-mean fields and 1 to 0).  Then dL/ddelta = -B^T lambda and
+    dL/dR_c = -lambda . dF/dR_c (dF/dR_c by central differences as well).
+    Returns (dL/ddelta, dL/dR_c, phi).  Cost O(n^6) memory: small n only."""
+    delta = _c(delta)
+    n = delta.shape[0]
+    N = n ** 3
+    phi, _ = dgp_solve(delta, a, omega_m, rc_h0, opts or Opts(rtol=1e-13, max_cycles=60))
+
+    def F(u, d, rc):
+        s0, _, alpha, _ = dgp_source(d, a, omega_m, rc)
+        return residual(dgp_op(alpha), u, s0, None, 1.0)[0].ravel()
+
+    su = step * max(1.0, np.abs(phi).max())
+    sd = step * max(1.0, np.abs(delta).max())
+    J = np.empty((N, N))
+    Bm = np.empty((N, N))
+    for q in range(N):
+        e = np.zeros(N)
+        e[q] = 1.0
+        e = e.reshape(delta.shape)
+        J[:, q] = (F(phi + su * e, delta, rc_h0) - F(phi - su * e, delta, rc_h0)) / (2 * su)
+        Bm[:, q] = (F(phi, delta + sd * e, rc_h0) - F(phi, delta - sd * e, rc_h0)) / (2 * sd)
+    gp = g.ravel() - g.mean()
+    lam = np.linalg.solve(J.T + np.full((N, N), 1.0 / N), gp)
+    dd = -(Bm.T @ lam)
+    sr = step * rc_h0
+    dFdr = (F(phi, delta, rc_h0 + sr) - F(phi, delta, rc_h0 - sr)) / (2 * sr)
+    return dd.reshape(delta.shape), float(-(lam @ dFdr)), phi

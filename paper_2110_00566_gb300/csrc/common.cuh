@@ -29,7 +29,30 @@ struct LevScal {
     double clamps;  // sqrt clamps counted in the last residual pass
     double mean;    // scratch mean (delta or u)
     double aux;     // scratch
+    float cf32;     // (float)(fshift - c), the smoother's constant for FP32 kernels
+    float pad_;
 };
+
+// update c (and the FP32 copy of fshift - c) from a finalising thread
+__device__ __forceinline__ void set_c(LevScal *sc, double c)
+{
+    sc->c = c;
+    sc->cf32 = (float)(sc->fshift - c);
+}
+__device__ __forceinline__ void set_c_fshift(LevScal *sc, double c, double fshift)
+{
+    sc->c = c;
+    sc->fshift = fshift;
+    sc->cf32 = (float)(fshift - c);
+}
+
+// the smoother's constant fshift - c in the kernel's precision
+template <typename T>
+__device__ __forceinline__ T smooth_cf(const LevScal *sc);
+template <>
+__device__ __forceinline__ double smooth_cf<double>(const LevScal *sc) { return sc->fshift - sc->c; }
+template <>
+__device__ __forceinline__ float smooth_cf<float>(const LevScal *sc) { return sc->cf32; }
 
 // reduction scratch shared by the reduction kernels of one pyramid
 struct RedBuf {
@@ -198,6 +221,10 @@ __device__ __forceinline__ T op_N(const OpK<T> &op, const LevK<T> &L, const Nb<T
             clamp = 1;
             return T(-0.75) * op.alpha;
         }
+        // FP64: the printed form needs no division and its absolute error
+        // (~1e-16 alpha) is far below the residuals the solve resolves; FP32
+        // keeps the rationalised form, which does not cancel for Sigma << alpha^2
+        if (sizeof(T) == 8) return T(0.75) * op.sgn_alpha * (sqrt(arg) - op.abs_alpha);
         return T(2) * op.sgn_alpha * sig / (op.abs_alpha + sqrt(arg));
     } else {
         const T dx = v.xp - v.xm, dy = v.yp - v.ym, dz = v.zp - v.zm;
@@ -364,6 +391,45 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], const RedBuf &rb, doub
 #pragma unroll
     for (int q = 0; q < NV; ++q) tot[q] = acc[q];
     if (tid == 0) *rb.counter = 0u;
+    return true;
+}
+
+// The same deterministic reduction over `nb` work tiles of one problem when
+// a persistent block processes tiles of several problems: tile `bid`
+// stores its block sums, and the block that stores the last one sums all
+// partials in tile order and returns true (totals valid in thread 0).
+template <int NV>
+__device__ __forceinline__ bool tile_sum(double (&v)[NV], double *partials, unsigned int *counter, unsigned bid,
+                                         unsigned nb, double (&tot)[NV])
+{
+    __shared__ double sh[32 * NV];
+    __shared__ bool last;
+    block_sum<NV>(v, sh);
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) partials[(size_t)bid * NV + q] = v[q];
+        __threadfence();
+        const unsigned t = atomicAdd(counter, 1u);
+        last = (t == nb - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+    const unsigned per = (nb + nthreads - 1) / nthreads;
+    const unsigned b0 = tid * per, b1 = min(nb, b0 + per);
+    for (unsigned b = b0; b < b1; ++b)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(partials + (size_t)b * NV + q);
+    block_sum<NV>(acc, sh);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] = acc[q];
+    if (tid == 0) *counter = 0u;
+    __syncthreads();
     return true;
 }
 

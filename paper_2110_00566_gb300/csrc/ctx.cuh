@@ -31,11 +31,11 @@ struct CudaFail {
 
 struct CycleKey {
     std::vector<int> state;  // cur[] of every level before the cycle
-    int pre, post, cycle, coarse_sweeps, nlev, prof;
+    int pre, post, cycle, coarse_sweeps, nlev, prof, norm;
     bool operator<(const CycleKey &o) const
     {
-        return std::tie(state, pre, post, cycle, coarse_sweeps, nlev, prof) <
-               std::tie(o.state, o.pre, o.post, o.cycle, o.coarse_sweeps, o.nlev, o.prof);
+        return std::tie(state, pre, post, cycle, coarse_sweeps, nlev, prof, norm) <
+               std::tie(o.state, o.pre, o.post, o.cycle, o.coarse_sweeps, o.nlev, o.prof, o.norm);
     }
 };
 
@@ -56,6 +56,7 @@ struct Pyramid {
     OpK<double> *opD = nullptr;        // device operator (FP64, coarsest)
     RedBuf rb{};
     void *block = nullptr;             // one allocation carved into the arrays
+    size_t block_bytes = 0;
     size_t bytes = 0;
     std::map<CycleKey, GraphEntry> graphs;
 
@@ -77,7 +78,8 @@ struct Pyramid {
     }
 };
 
-struct PmWork;  // particle-mesh workspace (pm.cu)
+struct PmWork;     // particle-mesh workspace (pm.cu)
+struct BatchWork;  // batched-ensemble workspace (batch.cu)
 
 struct ModelDesc {
     int model;         // 0 nDGP, 1 Kmouflage
@@ -109,6 +111,10 @@ struct mg_ctx {
     double *dscratch = nullptr;      // device scratch (64 doubles)
     mg::RedBuf rb{};                 // reduction buffer for stand-alone reductions
     mg::PmWork *pm = nullptr;
+    mg::BatchWork *batch = nullptr;
+    void *adj = nullptr;             // adjoint workspace (adjoint.cu)
+    size_t batch_partial_cap = 0;    // reduction tiles per instance
+    std::map<int, int> tuned_tx;     // autotuned tile width per level size
     // profiling of the finest-level smoother (events recorded in the graphs)
     int prof_on = 0;
     int prof_k = 0;                  // launches bracketed in the current cycle
@@ -128,6 +134,14 @@ size_t level_count(int n);
 bool valid_ng(int n);
 template <typename T>
 Pyramid<T> *get_pyramid(mg_ctx *ctx, int n, bool correction);
+// an uncached pyramid owned by the caller (batched solves), and its release
+template <typename T>
+Pyramid<T> *alloc_pyramid(mg_ctx *ctx, int n, bool correction);
+template <typename T>
+void release_pyramid(Pyramid<T> *P);
+int solve_batch(mg_ctx *ctx, int count, const mg_instance *inst, const mg_opts &o, mg_stats *stats);
+void batch_free(mg_ctx *ctx);
+void adj_release(mg_ctx *ctx);
 
 // entry/exit ordering with the caller's stream
 void enter(mg_ctx *ctx);

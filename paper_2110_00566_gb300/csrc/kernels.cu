@@ -1,10 +1,12 @@
 // Multigrid kernels of the GB300 MG-GLAM solvers (arXiv:2110.00566,
-// Sec. 3.2.1 for the FAS machinery, Sec. 3.2.3 / 3.2.4 for the operators).
-// Colour-split layout and the neighbour gather are described in common.cuh.
-// Every stencil kernel comes in a plain form (N(u)) and a correction form
-// (CORR: N(b + e) - N(b) with a frozen base field b, see op_dN).
+// Sec. 3.2.1 for the FAS machinery, Sec. 3.2.3 / 3.2.4 for the operators),
+// one level per launch.  Colour-split layout and the neighbour gather are
+// described in common.cuh, the per-cell bodies are in cells.cuh.  Every
+// stencil kernel comes in a plain form (N(u)) and a correction form (CORR:
+// N(b + e) - N(b) with a frozen base field b, see op_dN).
 #include <algorithm>
 
+#include "cells.cuh"
 #include "kernels.cuh"
 
 namespace mg {
@@ -60,27 +62,8 @@ OpK<T> make_opk(int model, double alpha, int nkmo, double gamma, double bterm)
     return o;
 }
 
-// N (plain) or dN (correction) at the colour-c cell (i, j, m) of row parity
-// p; also returns the sum of the 6 face neighbours of the unknown.
-template <typename T, bool CORR>
-__device__ __forceinline__ T cell_eval(const OpK<T> &op, const LevK<T> &L, const T *S, const T *O, const T *BS,
-                                       const T *BO, int i, int j, int m, int p, T s, int &cl, T &S6)
-{
-    Nb<T> v;
-    if (CORR) {
-        Nb<T> w;
-        gather2(v, w, S, O, BS, BO, L.n, L.half, i, j, m, p);
-        S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
-        return op_dN(op, L, v, w, s, cl);
-    }
-    gather(v, S, O, L.n, L.half, i, j, m, p);
-    S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
-    return op_N(op, L, v, s, cl);
-}
-
 // ---------------------------------------------------------------------------
 // smoother: one colour-simultaneous half-sweep (Eq. nonlinear_GS_DGP)
-//   u_new = (S6 - h^2 (N - c + f)) / 6,  f = f' + fshift
 // ---------------------------------------------------------------------------
 template <typename T, bool CORR>
 __global__ void __launch_bounds__(256)
@@ -88,28 +71,46 @@ k_smooth(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un,
          const T *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<T> L, const OpK<T> *__restrict__ opp,
          int colour, const T *__restrict__ Bc, const T *__restrict__ Bo)
 {
-    const OpK<T> op = *opp;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int i = blockIdx.z;
     if (m >= L.half || j >= L.n) return;
-    const int p = (colour + i + j) & 1;
-    const long long idx = row_of(i, j, L.n, L.half) + m;
-    int cl = 0;
-    T S6;
-    const T N = cell_eval<T, CORR>(op, L, Uc, Uo, Bc, Bo, i, j, m, p, __ldg(Sc + idx), cl, S6);
-    const T cf = (T)(sc->fshift - sc->c);
-    const T f = Fc ? __ldg(Fc + idx) : T(0);
-    Un[idx] = (S6 - L.h2 * (N + f + cf)) * T(1.0 / 6.0);
+    smooth_cell<T, CORR>(*opp, L, Uc, Uo, Un, Sc, Fc, smooth_cf<T>(sc), colour, Bc, Bo, i, j, m);
+}
+
+// two cells of a colour row per thread (rows of even length)
+template <typename T, bool CORR>
+__global__ void __launch_bounds__(256)
+k_smooth2(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un, const T *__restrict__ Sc,
+          const T *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<T> L, const OpK<T> *__restrict__ opp,
+          int colour, const T *__restrict__ Bc, const T *__restrict__ Bo)
+{
+    const int mp2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = blockIdx.z;
+    if (2 * mp2 >= L.half || j >= L.n) return;
+    smooth_pair<T, CORR>(*opp, L, Uc, Uo, Un, Sc, Fc, smooth_cf<T>(sc), colour, Bc, Bo, i, j, 2 * mp2);
 }
 
 template <typename T>
 void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, int colour, cudaStream_t st)
 {
-    const dim3 b = block_mj(L.half);
-    const dim3 g = grid_mj(L.half, L.n, b, L.n);
     const int nb = 1 - L.cur[colour];
     const LevK<T> K = make_levk<T>(L.n, L.h);
+    if (L.half % 2 == 0) {
+        const dim3 b = block_mj(L.half / 2);
+        const dim3 g = grid_mj(L.half / 2, L.n, b, L.n);
+        if (L.base[0])
+            k_smooth2<T, true><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour],
+                                                L.f[colour], L.sc, K, op, colour, L.base[colour], L.base[1 - colour]);
+        else
+            k_smooth2<T, false><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour],
+                                                 L.f[colour], L.sc, K, op, colour, nullptr, nullptr);
+        Lw->cur[colour] = nb;
+        return;
+    }
+    const dim3 b = block_mj(L.half);
+    const dim3 g = grid_mj(L.half, L.n, b, L.n);
     if (L.base[0])
         k_smooth<T, true><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], L.f[colour],
                                            L.sc, K, op, colour, L.base[colour], L.base[1 - colour]);
@@ -119,10 +120,40 @@ void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, in
     Lw->cur[colour] = nb;
 }
 
+// one half-sweep with an explicit block shape (bx x 256/bx) into the
+// alternate buffer, leaving the buffer state untouched (for the tile-shape
+// autotuner)
+template <typename T>
+void launch_smooth_shape(const LevArrays<T> &L, const OpK<T> *op, int colour, int bx, cudaStream_t st)
+{
+    const dim3 b(bx, 256 / bx, 1);
+    const dim3 g = grid_mj(L.half, L.n, b, L.n);
+    const int nb = 1 - L.cur[colour];
+    const LevK<T> K = make_levk<T>(L.n, L.h);
+    if (L.base[0])
+        k_smooth<T, true><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], L.f[colour],
+                                           L.sc, K, op, colour, L.base[colour], L.base[1 - colour]);
+    else
+        k_smooth<T, false><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour],
+                                            L.f[colour], L.sc, K, op, colour, nullptr, nullptr);
+}
+
+// finalise a residual pass: c_new = <N>, dc = c_new - c_old, eps^2 of the
+// residual with c_new (d_true = d_old + dc)
+__device__ __forceinline__ void finish_resid(LevScal *sc, const double (&tot)[4], double cnt, double c_old)
+{
+    const double c_new = tot[0] / cnt;
+    const double dc = c_new - c_old;
+    set_c(sc, c_new);
+    sc->dc = dc;
+    sc->eps2 = (tot[2] + 2.0 * dc * tot[1] + cnt * dc * dc) / cnt;
+    sc->sumN = tot[0];
+    sc->clamps = tot[3];
+}
+
 // ---------------------------------------------------------------------------
-// residual norm on one level (both colours):
-//   d = Lap u - N + c_old - f;  c_new = <N>;  d_true = d + (c_new - c_old)
-// optionally writes -d (old c) as FP32 for the correction solve's source
+// residual norm on one level (both colours); optionally writes -d (old c)
+// as FP32 for the correction solve's source
 // ---------------------------------------------------------------------------
 template <typename T, bool CORR>
 __global__ void __launch_bounds__(256)
@@ -137,40 +168,12 @@ k_resid_norm(const T *__restrict__ U0, const T *__restrict__ U1, const T *__rest
     const double c_old = sc->c;
     const double cshift = c_old - sc->fshift;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    if (m < L.half && j < L.n) {
-        for (int iz = blockIdx.z; iz < 2 * L.n; iz += gridDim.z) {
-            const int col = iz & 1, i = iz >> 1;
-            const T *Sa = col ? U1 : U0;
-            const T *Oa = col ? U0 : U1;
-            const int p = (col + i + j) & 1;
-            const long long idx = row_of(i, j, L.n, L.half) + m;
-            int cl = 0;
-            T S6;
-            const T N = cell_eval<T, CORR>(op, L, Sa, Oa, col ? B1 : B0, col ? B0 : B1, i, j, m, p,
-                                           __ldg((col ? S1 : S0) + idx), cl, S6);
-            const T u = __ldg(Sa + idx);
-            const T *Fa = col ? F1 : F0;
-            const T f = Fa ? __ldg(Fa + idx) : T(0);
-            const T dT = (S6 - T(6) * u) * L.inv_h2 - N - f;
-            const double d = (double)dT + cshift;
-            if (D0) (col ? D1 : D0)[idx] = (float)(-d);
-            acc[0] += (double)N;
-            acc[1] += d;
-            acc[2] += d * d;
-            acc[3] += (double)cl;
-        }
-    }
+    if (m < L.half && j < L.n)
+        for (int iz = blockIdx.z; iz < 2 * L.n; iz += gridDim.z)
+            resid_cell<T, CORR>(op, L, U0, U1, S0, S1, F0, F1, B0, B1, D0, D1, cshift, iz & 1, iz >> 1, j, m, acc);
     double tot[4];
-    if (grid_sum<4>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
-        const double cnt = (double)L.n * L.n * L.n;
-        const double c_new = tot[0] / cnt;
-        const double dc = c_new - c_old;
-        sc->c = c_new;
-        sc->dc = dc;
-        sc->eps2 = (tot[2] + 2.0 * dc * tot[1] + cnt * dc * dc) / cnt;
-        sc->sumN = tot[0];
-        sc->clamps = tot[3];
-    }
+    if (grid_sum<4>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0)
+        finish_resid(sc, tot, (double)L.n * L.n * L.n, c_old);
 }
 
 template <typename T>
@@ -191,10 +194,7 @@ void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb
 }
 
 // ---------------------------------------------------------------------------
-// fused residual + FAS restriction, one thread per coarse cell (I, J, K):
-//   the 8 children (2I+a, 2J+b, 2K+c) sit at split index K of the fine rows
-//   (2I+a, 2J+b), colour (a+b+c)&1.  Writes R u (coarse u and ur) and
-//   R d_old (into the coarse f, completed by the coarse-source kernel).
+// fused residual + FAS restriction, one thread per coarse cell (I, J, K)
 // ---------------------------------------------------------------------------
 template <typename T, bool CORR>
 __global__ void __launch_bounds__(256)
@@ -205,62 +205,19 @@ k_resid_restrict(const T *__restrict__ U0, const T *__restrict__ U1, const T *__
                  const T *__restrict__ B0, const T *__restrict__ B1)
 {
     const OpK<T> op = *opp;
-    const int nc = L.n / 2, halfc = nc / 2;
+    const int nc = L.n / 2;
     const int K = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const double c_old = sc->c;
     const double cshift = c_old - sc->fshift;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    if (K < nc && J < nc) {
-        for (int I = blockIdx.z; I < nc; I += gridDim.z) {
-            T su = T(0), sd = T(0);
-#pragma unroll
-            for (int ab = 0; ab < 4; ++ab) {
-                const int a = ab >> 1, b = ab & 1;
-                const int i = 2 * I + a, j = 2 * J + b;
-#pragma unroll
-                for (int cc = 0; cc < 2; ++cc) {
-                    const int col = (a + b + cc) & 1;
-                    const T *Sa = col ? U1 : U0;
-                    const T *Oa = col ? U0 : U1;
-                    const long long idx = row_of(i, j, L.n, L.half) + K;
-                    int cl = 0;
-                    T S6;
-                    const T N = cell_eval<T, CORR>(op, L, Sa, Oa, col ? B1 : B0, col ? B0 : B1, i, j, K, cc,
-                                                   __ldg((col ? S1 : S0) + idx), cl, S6);
-                    const T u = __ldg(Sa + idx);
-                    const T *Fa = col ? F1 : F0;
-                    const T f = Fa ? __ldg(Fa + idx) : T(0);
-                    const T dT = (S6 - T(6) * u) * L.inv_h2 - N - f;
-                    const double d = (double)dT + cshift;
-                    acc[0] += (double)N;
-                    acc[1] += d;
-                    acc[2] += d * d;
-                    acc[3] += (double)cl;
-                    su += u;
-                    sd += dT;
-                }
-            }
-            const int C = (I + J + K) & 1;
-            const long long cidx = row_of(I, J, nc, halfc) + (K >> 1);
-            const T Ru = su * T(0.125);
-            const T Rd = sd * T(0.125) + (T)cshift;
-            (C ? Uc1 : Uc0)[cidx] = Ru;
-            (C ? URc1 : URc0)[cidx] = Ru;
-            (C ? RDc1 : RDc0)[cidx] = Rd;
-        }
-    }
+    if (K < nc && J < nc)
+        for (int I = blockIdx.z; I < nc; I += gridDim.z)
+            rr_cell<T, CORR>(op, L, U0, U1, S0, S1, F0, F1, B0, B1, cshift, Uc0, Uc1, URc0, URc1, RDc0, RDc1, I, J, K,
+                             acc);
     double tot[4];
-    if (grid_sum<4>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
-        const double cnt = (double)L.n * L.n * L.n;
-        const double c_new = tot[0] / cnt;
-        const double dc = c_new - c_old;
-        sc->c = c_new;
-        sc->dc = dc;
-        sc->eps2 = (tot[2] + 2.0 * dc * tot[1] + cnt * dc * dc) / cnt;
-        sc->sumN = tot[0];
-        sc->clamps = tot[3];
-    }
+    if (grid_sum<4>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0)
+        finish_resid(sc, tot, (double)L.n * L.n * L.n, c_old);
 }
 
 template <typename T>
@@ -283,8 +240,8 @@ void launch_resid_restrict(const LevArrays<T> &Lf, LevArrays<T> &Lc, const OpK<T
 }
 
 // ---------------------------------------------------------------------------
-// coarse FAS source (Eq. general_pde_numerical_coarse), in place over R d:
-//   f' = Lap(Ru) - N(Ru) - (Rd_old + dc_fine);  c = fshift = <N(Ru)>
+// coarse FAS source (Eq. general_pde_numerical_coarse), in place over R d;
+// finalises c = fshift = <N(Ru)>
 // ---------------------------------------------------------------------------
 template <typename T, bool CORR>
 __global__ void __launch_bounds__(256)
@@ -297,31 +254,13 @@ k_coarse_source(const T *__restrict__ UR0, const T *__restrict__ UR1, const T *_
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const T dcf = (T)scf->dc;
     double acc[2] = {0.0, 0.0};
-    if (m < L.half && j < L.n) {
-        for (int iz = blockIdx.z; iz < 2 * L.n; iz += gridDim.z) {
-            const int col = iz & 1, i = iz >> 1;
-            const T *Sa = col ? UR1 : UR0;
-            const T *Oa = col ? UR0 : UR1;
-            const int p = (col + i + j) & 1;
-            const long long idx = row_of(i, j, L.n, L.half) + m;
-            int cl = 0;
-            T S6;
-            const T N = cell_eval<T, CORR>(op, L, Sa, Oa, col ? B1 : B0, col ? B0 : B1, i, j, m, p,
-                                           __ldg((col ? S1 : S0) + idx), cl, S6);
-            const T u = __ldg(Sa + idx);
-            T *Fa = col ? F1 : F0;
-            const T rd = Fa[idx];
-            Fa[idx] = (S6 - T(6) * u) * L.inv_h2 - N - (rd + dcf);
-            acc[0] += (double)N;
-            acc[1] += (double)cl;
-        }
-    }
+    if (m < L.half && j < L.n)
+        for (int iz = blockIdx.z; iz < 2 * L.n; iz += gridDim.z)
+            cs_cell<T, CORR>(op, L, UR0, UR1, S0, S1, F0, F1, B0, B1, dcf, iz & 1, iz >> 1, j, m, acc);
     double tot[2];
     if (grid_sum<2>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
-        const double cnt = (double)L.n * L.n * L.n;
-        const double c = tot[0] / cnt;
-        scc->c = c;
-        scc->fshift = c;
+        const double c = tot[0] / ((double)L.n * L.n * L.n);
+        set_c_fshift(scc, c, c);
         scc->dc = 0.0;
         scc->sumN = tot[0];
         scc->clamps = tot[1];
@@ -345,47 +284,18 @@ void launch_coarse_source(const LevArrays<T> &Lf, const LevArrays<T> &Lc, const 
 }
 
 // ---------------------------------------------------------------------------
-// prolongation + correction (Eq. solution_correction): u += P(uH - urH),
-// weights 27, 9, 3, 1 over 64 for the parent, face, edge and vertex cells
-// on the fine cell's side.
+// prolongation + correction (Eq. solution_correction)
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T coarse_e(const T *__restrict__ A0, const T *__restrict__ A1, const T *__restrict__ B0,
-                                      const T *__restrict__ B1, int I, int J, int K, int nc, int halfc)
-{
-    const long long q = row_of(I, J, nc, halfc) + (K >> 1);
-    return ((I + J + K) & 1) ? (__ldg(A1 + q) - __ldg(B1 + q)) : (__ldg(A0 + q) - __ldg(B0 + q));
-}
-
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_prolong(T *U0, T *U1, const T *__restrict__ UH0, const T *__restrict__ UH1, const T *__restrict__ RH0,
           const T *__restrict__ RH1, int n)
 {
-    const int half = n / 2, nc = n / 2, halfc = nc / 2;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int iz = blockIdx.z;
-    const int col = iz & 1, i = iz >> 1;
-    if (m >= half || j >= n) return;
-    const int p = (col + i + j) & 1;
-    const int k = 2 * m + p;
-    const int I = i >> 1, J = j >> 1, K = k >> 1;
-    const int I2 = (i & 1) ? (I + 1 == nc ? 0 : I + 1) : (I == 0 ? nc - 1 : I - 1);
-    const int J2 = (j & 1) ? (J + 1 == nc ? 0 : J + 1) : (J == 0 ? nc - 1 : J - 1);
-    const int K2 = (k & 1) ? (K + 1 == nc ? 0 : K + 1) : (K == 0 ? nc - 1 : K - 1);
-    const T e000 = coarse_e(UH0, UH1, RH0, RH1, I, J, K, nc, halfc);
-    const T e100 = coarse_e(UH0, UH1, RH0, RH1, I2, J, K, nc, halfc);
-    const T e010 = coarse_e(UH0, UH1, RH0, RH1, I, J2, K, nc, halfc);
-    const T e001 = coarse_e(UH0, UH1, RH0, RH1, I, J, K2, nc, halfc);
-    const T e110 = coarse_e(UH0, UH1, RH0, RH1, I2, J2, K, nc, halfc);
-    const T e101 = coarse_e(UH0, UH1, RH0, RH1, I2, J, K2, nc, halfc);
-    const T e011 = coarse_e(UH0, UH1, RH0, RH1, I, J2, K2, nc, halfc);
-    const T e111 = coarse_e(UH0, UH1, RH0, RH1, I2, J2, K2, nc, halfc);
-    const T corr = (T(27) * e000 + T(9) * (e100 + e010 + e001) + T(3) * (e110 + e101 + e011) + e111) * T(1.0 / 64.0);
-    T *Ua = col ? U1 : U0;
-    const long long idx = row_of(i, j, n, half) + m;
-    Ua[idx] += corr;
+    if (m >= n / 2 || j >= n) return;
+    prolong_cell<T>(U0, U1, UH0, UH1, RH0, RH1, n, iz & 1, iz >> 1, j, m);
 }
 
 template <typename T>
@@ -397,98 +307,15 @@ void launch_prolong(const LevArrays<T> &Lf, const LevArrays<T> &Lc, cudaStream_t
 }
 
 // ---------------------------------------------------------------------------
-// coarsest level: one CTA, FP64 in shared memory (natural layout),
-// `sweeps` times { c = <N(u)>; colour 0; colour 1 }
+// coarsest level: one CTA, FP64 in shared memory
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void gather_nat(Nb<double> &v, const double *u, int n, int i, int j, int k)
-{
-    const int ip = wrap_p(i, n), im = wrap_m(i, n), jp = wrap_p(j, n), jm = wrap_m(j, n);
-    const int kp = wrap_p(k, n), km = wrap_m(k, n);
-#define U_(a, b, c) u[((a) * n + (b)) * n + (c)]
-    v.xp = U_(ip, j, k); v.xm = U_(im, j, k);
-    v.yp = U_(i, jp, k); v.ym = U_(i, jm, k);
-    v.zp = U_(i, j, kp); v.zm = U_(i, j, km);
-    v.xpyp = U_(ip, jp, k); v.xmym = U_(im, jm, k); v.xpym = U_(ip, jm, k); v.xmyp = U_(im, jp, k);
-    v.xpzp = U_(ip, j, kp); v.xmzm = U_(im, j, km); v.xpzm = U_(ip, j, km); v.xmzp = U_(im, j, kp);
-    v.ypzp = U_(i, jp, kp); v.ymzm = U_(i, jm, km); v.ypzm = U_(i, jp, km); v.ymzp = U_(i, jm, kp);
-#undef U_
-}
-
-template <bool CORR>
-__device__ __forceinline__ double nat_eval(const OpK<double> &op, const LevK<double> &L, const double *u,
-                                           const double *bs, int n, int i, int j, int k, double s, double &S6)
-{
-    Nb<double> v;
-    gather_nat(v, u, n, i, j, k);
-    S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
-    int cl = 0;
-    if (CORR) {
-        Nb<double> w;
-        gather_nat(w, bs, n, i, j, k);
-        return op_dN(op, L, v, w, s, cl);
-    }
-    return op_N(op, L, v, s, cl);
-}
-
 template <typename T, bool CORR>
 __global__ void __launch_bounds__(512)
 k_coarsest(T *U0, T *U1, const T *S0, const T *S1, const T *F0, const T *F1, LevScal *sc, int n, double h,
            const OpK<double> *__restrict__ opp, int sweeps, const T *B0, const T *B1)
 {
-    const OpK<double> op = *opp;
     extern __shared__ double smem[];
-    const int n3 = n * n * n, half = n / 2;
-    double *u = smem, *s = smem + n3, *f = smem + 2 * n3, *un = smem + 3 * n3, *bs = smem + 4 * n3;
-    __shared__ double shred[32];
-    __shared__ double cbc;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int q = tid; q < n3; q += nt) {
-        const int i = q / (n * n), j = (q / n) % n, k = q % n;
-        const int col = (i + j + k) & 1;
-        const long long si = row_of(i, j, n, half) + (k >> 1);
-        u[q] = (double)(col ? U1 : U0)[si];
-        s[q] = (double)(col ? S1 : S0)[si];
-        const T *Fa = col ? F1 : F0;
-        f[q] = Fa ? (double)Fa[si] : 0.0;
-        if (CORR) bs[q] = (double)(col ? B1 : B0)[si];
-    }
-    __syncthreads();
-    const LevK<double> L = make_levk<double>(n, h);
-    const double fshift = sc->fshift;
-    double c = sc->c;
-    for (int it = 0; it < sweeps; ++it) {
-        double acc[1] = {0.0};
-        for (int q = tid; q < n3; q += nt) {
-            double S6;
-            acc[0] += nat_eval<CORR>(op, L, u, bs, n, q / (n * n), (q / n) % n, q % n, s[q], S6);
-        }
-        block_sum<1>(acc, shred);
-        if (tid == 0) cbc = acc[0] / n3;
-        __syncthreads();
-        c = cbc;
-        for (int colour = 0; colour < 2; ++colour) {
-            for (int q = tid; q < n3; q += nt) {
-                const int i = q / (n * n), j = (q / n) % n, k = q % n;
-                if (((i + j + k) & 1) != colour) continue;
-                double S6;
-                const double N = nat_eval<CORR>(op, L, u, bs, n, i, j, k, s[q], S6);
-                un[q] = (S6 - L.h2 * (N - c + fshift + f[q])) * (1.0 / 6.0);
-            }
-            __syncthreads();
-            for (int q = tid; q < n3; q += nt) {
-                const int i = q / (n * n), j = (q / n) % n, k = q % n;
-                if (((i + j + k) & 1) == colour) u[q] = un[q];
-            }
-            __syncthreads();
-        }
-    }
-    for (int q = tid; q < n3; q += nt) {
-        const int i = q / (n * n), j = (q / n) % n, k = q % n;
-        const int col = (i + j + k) & 1;
-        const long long si = row_of(i, j, n, half) + (k >> 1);
-        (col ? U1 : U0)[si] = (T)u[q];
-    }
-    if (tid == 0) sc->c = c;
+    coarsest_block<T, CORR>(U0, U1, S0, S1, F0, F1, sc, n, h, *opp, sweeps, B0, B1, smem);
 }
 
 template <typename T>
@@ -512,19 +339,11 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_restrict_plain(const T *__restrict__ F0, const T *__restrict__ F1, T *__restrict__ C0, T *__restrict__ C1, int nf)
 {
-    const int nc = nf / 2, halfc = nc / 2, halff = nf / 2;
+    const int nc = nf / 2;
     const int K = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
-    const int I = blockIdx.z;
     if (K >= nc || J >= nc) return;
-    T acc = T(0);
-#pragma unroll
-    for (int ab = 0; ab < 4; ++ab) {
-        const long long r = row_of(2 * I + (ab >> 1), 2 * J + (ab & 1), nf, halff) + K;
-        acc += __ldg(F0 + r) + __ldg(F1 + r);
-    }
-    const long long cidx = row_of(I, J, nc, halfc) + (K >> 1);
-    (((I + J + K) & 1) ? C1 : C0)[cidx] = acc * T(0.125);
+    restrict_cell<T>(F0, F1, C0, C1, nf, blockIdx.z, J, K);
 }
 
 template <typename T>
@@ -679,7 +498,10 @@ __global__ void k_set_corr_scalars(LevScal *sc32, const LevScal *__restrict__ sc
     const int l = threadIdx.x;
     if (l >= nlev) return;
     LevScal z{};
-    if (l == 0) z.fshift = -sc64->dc;
+    if (l == 0) {
+        z.fshift = -sc64->dc;
+        z.cf32 = (float)z.fshift;
+    }
     sc32[l] = z;
 }
 
@@ -694,6 +516,7 @@ void launch_set_corr_scalars(LevScal *sc32, const LevScal *sc64, int nlev32, cud
 #define INST(T)                                                                                              \
     template OpK<T> make_opk<T>(int, double, int, double, double);                                         \
     template void launch_smooth<T>(const LevArrays<T> &, LevArrays<T> *, const OpK<T> *, int, cudaStream_t); \
+    template void launch_smooth_shape<T>(const LevArrays<T> &, const OpK<T> *, int, int, cudaStream_t);      \
     template void launch_resid_norm<T>(const LevArrays<T> &, const OpK<T> *, const RedBuf &, cudaStream_t,   \
                                        float *const *);                                                     \
     template void launch_resid_restrict<T>(const LevArrays<T> &, LevArrays<T> &, const OpK<T> *,              \

@@ -29,6 +29,8 @@ template <typename T> OpK<T> make_opk(int model, double alpha, int nkmo, double 
 
 template <typename T>
 void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, int colour, cudaStream_t st);
+template <typename T>
+void launch_smooth_shape(const LevArrays<T> &L, const OpK<T> *op, int colour, int bx, cudaStream_t st);
 // residual norm; with D set also writes -d (with the old c) as FP32,
 // colour-split
 template <typename T>

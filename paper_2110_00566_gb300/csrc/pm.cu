@@ -402,15 +402,6 @@ int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats)
     return rc;
 }
 
-int mg_solve_adjoint(mg_ctx *ctx, const mg_grid *g, const mg_dgp_params *p, const mg_opts *opts, const double *phi,
-                     const double *delta, const double *dL_dphi, double *dL_ddelta_out, double *dL_drc_out,
-                     mg_stats *stats)
-{
-    (void)g; (void)p; (void)opts; (void)phi; (void)delta; (void)dL_dphi; (void)dL_ddelta_out; (void)dL_drc_out;
-    (void)stats;
-    return set_err(ctx, MG_ERR_ARG, "mg_solve_adjoint: not available in this build");
-}
-
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

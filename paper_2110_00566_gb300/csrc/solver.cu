@@ -100,7 +100,7 @@ bool valid_ng(int n)
 static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
 template <typename T>
-static void free_pyramid(Pyramid<T> *P)
+void release_pyramid(Pyramid<T> *P)
 {
     if (!P) return;
     for (auto &g : P->graphs)
@@ -118,11 +118,8 @@ template <>
 std::map<int, Pyramid<float> *> &pyr_map<float>(mg_ctx *ctx, bool corr) { return corr ? ctx->p32c : ctx->p32; }
 
 template <typename T>
-Pyramid<T> *get_pyramid(mg_ctx *ctx, int n, bool correction)
+Pyramid<T> *alloc_pyramid(mg_ctx *ctx, int n, bool correction)
 {
-    auto &mp = pyr_map<T>(ctx, correction);
-    auto it = mp.find(n);
-    if (it != mp.end()) return it->second;
     auto *P = new Pyramid<T>();
     P->n0 = n;
     P->nlev = (int)level_count(n);
@@ -187,12 +184,27 @@ Pyramid<T> *get_pyramid(mg_ctx *ctx, int n, bool correction)
         L.sc = P->scal + l;
     }
     P->bytes = total + small;
+    P->block_bytes = total;
+    return P;
+}
+
+template <typename T>
+Pyramid<T> *get_pyramid(mg_ctx *ctx, int n, bool correction)
+{
+    auto &mp = pyr_map<T>(ctx, correction);
+    auto it = mp.find(n);
+    if (it != mp.end()) return it->second;
+    Pyramid<T> *P = alloc_pyramid<T>(ctx, n, correction);
     mp[n] = P;
     return P;
 }
 
 template Pyramid<double> *get_pyramid<double>(mg_ctx *, int, bool);
 template Pyramid<float> *get_pyramid<float>(mg_ctx *, int, bool);
+template Pyramid<double> *alloc_pyramid<double>(mg_ctx *, int, bool);
+template Pyramid<float> *alloc_pyramid<float>(mg_ctx *, int, bool);
+template void release_pyramid<double>(Pyramid<double> *);
+template void release_pyramid<float>(Pyramid<float> *);
 
 // ---------------------------------------------------------------------------
 // the FAS cycle (Sec. 3.2.1): pre-smooth, fused residual + restriction,
@@ -295,19 +307,21 @@ static long long cycle_updates(const Pyramid<T> &P, const mg_opts &o, int l, int
 // One cycle followed by the finest residual norm, from a captured graph
 // when use_graph is set (one graph per pointer state of the ping-pong
 // buffers; the state returns to itself when pre + post is even).
+// (norm = false: the cycle alone, for the inner cycles of the mixed solve,
+// whose convergence is judged by the FP64 defect)
 template <typename T>
-static void cycle_and_norm(mg_ctx *ctx, Pyramid<T> &P, const mg_opts &o)
+static void cycle_and_norm(mg_ctx *ctx, Pyramid<T> &P, const mg_opts &o, bool norm = true)
 {
     auto record = [&]() {
         ctx->prof_k = 0;
         run_cycle(ctx, P, o, 0, o.cycle);
-        launch_resid_norm<T>(P.L[0], P.opT, P.rb, ctx->stream);
+        if (norm) launch_resid_norm<T>(P.L[0], P.opT, P.rb, ctx->stream);
     };
     if (!o.use_graph) {
         record();
         return;
     }
-    CycleKey key{P.state(), o.pre, o.post, o.cycle, o.coarse_sweeps, P.nlev, ctx->prof_on};
+    CycleKey key{P.state(), o.pre, o.post, o.cycle, o.coarse_sweeps, P.nlev, ctx->prof_on, norm ? 1 : 0};
     auto it = P.graphs.find(key);
     if (it == P.graphs.end()) {
         const std::vector<int> pre_state = P.state();
@@ -493,9 +507,9 @@ int solve_mixed(mg_ctx *ctx, int n, const ModelDesc &md, const double *delta, do
         MG_CK(cudaMemsetAsync(E0.U(0), 0, sizeof(float) * E0.ncol, s));
         MG_CK(cudaMemsetAsync(E0.U(1), 0, sizeof(float) * E0.ncol, s));
         for (int k = 0; k < inner && cyc < o.max_cycles; ++k) {
-            cycle_and_norm(ctx, P32, o);
+            cycle_and_norm(ctx, P32, o, false);
             ++cyc;
-            launches += per_launch;
+            launches += per_launch - 1;
             if (ctx->prof_on) {
                 MG_CK(cudaStreamSynchronize(s));
                 loc.fine_smooth_ms += prof_collect(ctx);
@@ -646,10 +660,12 @@ void mg_ctx_destroy(mg_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    for (auto &p : ctx->p64) free_pyramid(p.second);
-    for (auto &p : ctx->p32) free_pyramid(p.second);
-    for (auto &p : ctx->p64c) free_pyramid(p.second);
-    for (auto &p : ctx->p32c) free_pyramid(p.second);
+    for (auto &p : ctx->p64) release_pyramid(p.second);
+    for (auto &p : ctx->p32) release_pyramid(p.second);
+    for (auto &p : ctx->p64c) release_pyramid(p.second);
+    for (auto &p : ctx->p32c) release_pyramid(p.second);
+    batch_free(ctx);
+    adj_release(ctx);
     mg_pm_free(ctx);
     for (int q = 0; q < mg_ctx::NSTAGE; ++q)
         if (ctx->stage[q]) cudaFree(ctx->stage[q]);
@@ -708,6 +724,20 @@ int mg_solve_dgp(mg_ctx *ctx, int count, const mg_instance *inst, const mg_opts 
             return set_err(ctx, MG_ERR_ARG, "instance %d: a, omega_m and rc_h0 must be > 0", q);
     }
     int worst = MG_OK;
+    // the batched form: MIXED precision, several instances, device arrays
+    bool batched = count > 1 && o.precision == MG_PREC_MIXED && (o.pre + o.post) % 2 == 0;
+    for (int q = 0; batched && q < count; ++q)
+        batched = is_device_ptr(inst[q].delta) && is_device_ptr(inst[q].phi);
+    if (batched) {
+        try {
+            enter(ctx);
+            worst = solve_batch(ctx, count, inst, o, stats);
+            leave(ctx);
+        } catch (CudaFail &f) {
+            return f.code;
+        }
+        return worst;
+    }
     try {
         enter(ctx);
         for (int q = 0; q < count; ++q) {
@@ -789,6 +819,7 @@ static int op_smooth_t(mg_ctx *ctx, const mg_op_params *op, int n, double h, con
     }
     LevScal hs{};
     hs.c = c;
+    hs.cf32 = (float)(-c);
     memcpy(ctx->hpin, &hs, sizeof hs);
     MG_CK(cudaMemcpyAsync(L.sc, ctx->hpin, sizeof hs, cudaMemcpyHostToDevice, st));
     launch_smooth<T>(L, &L, P.opT, colour, st);
@@ -822,6 +853,7 @@ static int op_smooth_corr_t(mg_ctx *ctx, const mg_op_params *op, int n, double h
     }
     LevScal hs{};
     hs.c = c;
+    hs.cf32 = (float)(-c);
     memcpy(ctx->hpin, &hs, sizeof hs);
     MG_CK(cudaMemcpyAsync(L.sc, ctx->hpin, sizeof hs, cudaMemcpyHostToDevice, st));
     launch_smooth<float>(L, &L, P.opT, colour, st);

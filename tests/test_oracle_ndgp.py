@@ -346,3 +346,38 @@ def test_sphere_shape(orc):
             r = np.sqrt(m ** 2 + 0.5)
             expect = dphidr(r) * m / r
             assert g == pytest.approx(expect, rel=0.08), (rc, m, g, expect)
+
+
+# ------------------------------------------------------- reference gradient
+
+def test_reference_gradient_matches_finite_differences(orc):
+    """The oracle's dense-Jacobian gradient of L = <g, phi> equals central
+    differences of the oracle's own solution map, in delta along random
+    directions and in R_c (strongly nonlinear field, 8^3)."""
+    n, a, om, rc = 8, 1.0, 0.3, 1.0
+    delta = 3.0 * inputs.white_noise(n, 201)
+    g = inputs.white_noise(n, 202)
+    dd, dr, phi = orc.dgp_gradient(delta, a, om, rc, g)
+    opts = orc.Opts(rtol=1e-14, max_cycles=80)
+    L = lambda d, r: float(np.sum(g * orc.dgp_solve(d, a, om, r, opts)[0]))
+    for seed in (203, 204, 205):
+        v = inputs.white_noise(n, seed)
+        eps = 1e-4
+        fd = (L(delta + eps * v, rc) - L(delta - eps * v, rc)) / (2 * eps)
+        assert float(np.sum(dd * v)) == pytest.approx(fd, rel=1e-6, abs=1e-10)
+    fd = (L(delta, rc * (1 + 1e-5)) - L(delta, rc * (1 - 1e-5))) / (2e-5 * rc)
+    assert dr == pytest.approx(fd, rel=1e-5)
+
+
+def test_reference_gradient_linear_limit(orc):
+    """For small delta the solution map is the linear Poisson solve
+    Lap phi = Omega_m a^-1 Pi delta / beta, whose Green's function is
+    symmetric, so dL/ddelta = (Omega_m/(a beta)) Pi G(Pi g)."""
+    n, a, om, rc = 8, 1.0, 0.3, 2.0
+    delta = 1e-7 * inputs.white_noise(n, 206)
+    g = inputs.white_noise(n, 207)
+    dd, _, _ = orc.dgp_gradient(delta, a, om, rc, g)
+    beta = orc.beta_dgp(a, om, rc)
+    ref = om / (a * beta) * orc.fft_poisson(g - g.mean())
+    ref -= ref.mean()
+    assert np.abs(dd - ref).max() < 1e-6 * np.abs(ref).max()
