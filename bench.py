@@ -57,6 +57,9 @@ def args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-forms", action="store_true")
+    p.add_argument("--inner", type=int, default=0, help="FP32 cycles per FP64 defect (0: library default)")
+    p.add_argument("--batch", type=int, default=64, help="instances of the batched form (0: skip)")
+    p.add_argument("--adj-ng", type=int, default=128, help="mesh of the adjoint form (0: skip)")
     return p.parse_args()
 
 
@@ -217,6 +220,8 @@ def main():
         bracket the library's stream (ordered by events at entry/exit)."""
         prec = B.MG_PREC_FP64 if precision == "fp64" else B.MG_PREC_MIXED
         o = B.opts(rtol=a.rtol, precision=prec, max_cycles=60)
+        if a.inner > 0:
+            o.inner_cycles = a.inner
         phi = torch.zeros_like(delta)
         inst = dict(ng=ng, box_mpch=a.box, a=1.0, omega_m=0.3, rc_h0=a.rc, delta=delta, phi=phi)
         for _ in range(a.warmup):
@@ -291,11 +296,99 @@ def main():
                 "peak_source": peak_src, "avg_launch_ms": ms, "launches": r["fine_launches"],
                 "alg_bytes_per_launch": alg}
 
+    def batched():
+        """Emulator ensemble: a.batch independent solves, N uniform over
+        {64, 96, 128, 192, 256}, L = N Mpc/h, N/2 particles per side,
+        Zel'dovich at z = 0 with sigma_8 ~ U[0.7, 0.9], H0 r_c log-uniform in
+        [0.5, 10] (seed 4 + rank); mixed precision.  The batched call (one
+        persistent kernel) against a loop of single solves."""
+        import numpy as np
+        from paper_2110_00566_gb300 import inputs
+        rng = np.random.default_rng(4 + rank)
+        insts, seq = [], []
+        for q in range(a.batch):
+            n = int(rng.choice([64, 96, 128, 192, 256]))
+            sig8 = float(rng.uniform(0.7, 0.9))
+            rc = float(np.exp(rng.uniform(np.log(0.5), np.log(10.0))))
+            p_, _ = inputs.zeldovich(n // 2, n, float(n), inputs.pk_cutoff(sigma8=sig8), 1.0, seed=100 + q)
+            d = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+            B.pm_cic_deposit(ctx, n, torch.from_numpy(p_).to(dev), d)
+            insts.append(dict(ng=n, box_mpch=float(n), a=1.0, omega_m=0.3, rc_h0=rc, delta=d,
+                              phi=torch.zeros_like(d)))
+            seq.append(dict(insts[-1], phi=torch.zeros_like(d)))
+        o = B.opts(rtol=a.rtol, precision=B.MG_PREC_MIXED, max_cycles=60)
+        if a.inner > 0:
+            o.inner_cycles = a.inner
+        for _ in range(max(1, a.warmup)):
+            B.mg_solve_dgp(ctx, insts, o)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        upd = 0
+        for _ in range(a.steps):
+            _, st = B.mg_solve_dgp(ctx, insts, o)
+            upd += sum(s.cell_updates for s in st)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms_b = e0.elapsed_time(e1) / a.steps
+        for inst in seq:
+            B.mg_solve_dgp(ctx, [inst], o)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for _ in range(a.steps):
+            for inst in seq:
+                B.mg_solve_dgp(ctx, [inst], o)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms_s = e0.elapsed_time(e1) / a.steps
+        worst = max(float(torch.linalg.vector_norm(x["phi"] - y["phi"]) / torch.linalg.vector_norm(y["phi"]))
+                    for x, y in zip(insts, seq))
+        cells = sum(x["ng"] ** 3 for x in insts)
+        return {"value": upd / a.steps / (ms_b * 1e-3) / 1e9, "unit": UNIT, "instances": a.batch,
+                "total_cells": cells, "ms_per_batch": ms_b, "ms_sequential_loop": ms_s,
+                "speedup_vs_sequential": ms_s / ms_b, "phi_rel_l2_vs_sequential_max": worst,
+                "sizes": sorted({x["ng"] for x in insts}), "launch": "one persistent cooperative kernel, graph-captured"}
+
+    def adjoint():
+        """Backward/forward: the FP64 adjoint solve (mg_solve_adjoint) vs the
+        FP64 forward solve at a.adj_ng^3 (CIC of a Zel'dovich load, L = 2 N)."""
+        import numpy as np
+        from paper_2110_00566_gb300 import inputs
+        n = a.adj_ng
+        p_, _ = inputs.zeldovich(n, n, 2.0 * n, inputs.pk_cutoff(), 1.0, seed=5)
+        d = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+        B.pm_cic_deposit(ctx, n, torch.from_numpy(p_).to(dev), d)
+        phi = torch.zeros_like(d)
+        g = torch.from_numpy(inputs.white_noise(n, 6)).to(dev)
+        out = torch.empty_like(d)
+        o = B.opts(rtol=a.rtol, max_cycles=60)
+        inst = dict(ng=n, box_mpch=2.0 * n, a=1.0, omega_m=0.3, rc_h0=a.rc, delta=d, phi=phi)
+        for _ in range(2):
+            B.mg_solve_dgp(ctx, [inst], o)
+            B.mg_solve_adjoint(ctx, n, 2.0 * n, 1.0, 0.3, a.rc, phi, d, g, out, o)
+        torch.cuda.synchronize(dev)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        for _ in range(a.steps):
+            B.mg_solve_dgp(ctx, [inst], o)
+        e1.record()
+        cyc = 0
+        for _ in range(a.steps):
+            _, _, st = B.mg_solve_adjoint(ctx, n, 2.0 * n, 1.0, 0.3, a.rc, phi, d, g, out, o)
+            cyc = st.cycles
+        e2.record()
+        torch.cuda.synchronize(dev)
+        fwd, bwd = e0.elapsed_time(e1) / a.steps, e1.elapsed_time(e2) / a.steps
+        return {"ng": n, "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+                "adjoint_cycles": cyc, "precision": "fp64"}
+
     primary = timed(a.precision)
     second = None
     if not a.no_forms:
         second = timed("mixed" if a.precision == "fp64" else "fp64")
     e2e_primary = None if a.no_e2e else e2e(primary)
+    batch_form = batched() if (a.batch > 0 and not a.no_forms) else None
+    adj_form = adjoint() if (a.adj_ng > 0 and not a.no_forms) else None
 
     if rank != 0:
         if dist:
@@ -315,6 +408,10 @@ def main():
                        "final_eps_over_eps_ref": st1.eps[st1.n_eps - 1] / st1.eps_ref,
                        "gpu_launches": second["launches"], "clocks": second["clocks"],
                        "roofline": roofline(second, name, fp64_tf)}
+    if batch_form is not None:
+        forms["batched"] = batch_form
+    if adj_form is not None:
+        forms["adjoint"] = adj_form
     cb = None if a.no_cpu else cpu_baseline(delta.cpu().numpy(), a)
     line = {"metric": METRIC, "value": primary["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": primary["ms_per_step"], "higher_is_better": True,

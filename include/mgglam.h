@@ -165,9 +165,13 @@ typedef struct {
  * red-black update of Eq. nonlinear_GS_DGP.  delta - <delta> is used; the
  * periodic system is made compatible by L(u) = Lap u - N(u) + <N(u)>, and
  * the result has <phi> = 0.
- * count >= 1 independent instances (sizes may differ); count > 1 is the
- * batched form: all instances advance together, one fused launch per
- * multigrid step across the batch.  stats: `count` records (or NULL).
+ * count >= 1 independent instances (sizes may differ).  count > 1 with
+ * precision MG_PREC_MIXED, device-resident delta/phi and pre + post even is
+ * the batched form: one persistent cooperative kernel runs the whole
+ * mixed-precision solve of every instance, walking the tiles of all
+ * instances still iterating in each phase; an instance leaves the work
+ * lists when it meets its tolerance.  Other count > 1 calls solve the
+ * instances one after another.  stats: `count` records (or NULL).
  * Returns MG_OK, MG_WARN_NOT_CONVERGED, MG_ERR_ARG, MG_ERR_CUDA,
  * MG_ERR_NONFINITE or MG_ERR_OOM.
  */

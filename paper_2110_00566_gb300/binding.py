@@ -339,3 +339,36 @@ def mg_op_prolong_add(ctx, precision, n, u_fine, uc, urc):
 
 def mg_op_coarsest(ctx, op, n, h, u, s, f, sweeps):
     return ctx._rc(lib().mg_op_coarsest(ctx.h, C.byref(op), n, h, _ptr(u), _ptr(s), _ptr(f), sweeps))
+
+
+# ---------------------------------------------------------------- autograd
+
+def autograd_solve():
+    """torch.autograd.Function over the nDGP solve: forward calls
+    mg_solve_dgp, backward calls mg_solve_adjoint (gradients with respect to
+    delta and to the scalar H0 r_c).  Usage:
+        phi = autograd_solve().apply(delta, rc, ctx, a, omega_m, box_mpch, opts)
+    with delta a CUDA FP64 tensor (ng^3) and rc a 0-d FP64 tensor."""
+    import torch
+
+    class MGSolveFn(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, delta, rc, mgctx, a, omega_m, box_mpch, o):
+            phi = torch.zeros_like(delta)
+            ng = int(delta.shape[0])
+            mg_solve_dgp(mgctx, [dict(ng=ng, box_mpch=box_mpch, a=a, omega_m=omega_m, rc_h0=float(rc),
+                                      delta=delta.contiguous(), phi=phi)], o)
+            fctx.save_for_backward(delta, phi)
+            fctx.args = (mgctx, a, omega_m, box_mpch, float(rc), o)
+            return phi
+
+        @staticmethod
+        def backward(fctx, gphi):
+            delta, phi = fctx.saved_tensors
+            mgctx, a, omega_m, box_mpch, rc, o = fctx.args
+            out = torch.empty_like(delta)
+            _, drc, _ = mg_solve_adjoint(mgctx, int(delta.shape[0]), box_mpch, a, omega_m, rc, phi,
+                                         delta.contiguous(), gphi.contiguous(), out, o)
+            return out, torch.tensor(drc, dtype=torch.float64), None, None, None, None, None
+
+    return MGSolveFn

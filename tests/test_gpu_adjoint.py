@@ -56,3 +56,28 @@ def test_adjoint_matches_finite_differences_of_the_gpu_solve(B, ctx):
     assert dr == pytest.approx(fd, rel=1e-5)
     # the adjoint solve converges like the forward one (a handful of cycles)
     assert st.cycles <= 20
+
+
+def test_autograd_function(B, ctx):
+    """The autograd wrapper's backward equals mg_solve_adjoint, and a loss
+    gradient along a direction matches central differences of the forward."""
+    n, a, om = 16, 1.0, 0.3
+    dev = torch.device("cuda", 0)
+    delta = torch.from_numpy(2.0 * inputs.white_noise(n, 601)).to(dev).requires_grad_(True)
+    rc = torch.tensor(1.5, dtype=torch.float64, requires_grad=True)
+    g = torch.from_numpy(inputs.white_noise(n, 602)).to(dev)
+    Fn = B.autograd_solve()
+    o = B.opts(rtol=1e-13, max_cycles=60)
+    phi = Fn.apply(delta, rc, ctx, a, om, float(n), o)
+    loss = (g * phi).sum()
+    loss.backward()
+    dd = delta.grad.cpu().numpy()
+    ref = np.empty((n,) * 3)
+    _, drc, _ = B.mg_solve_adjoint(ctx, n, float(n), a, om, 1.5, phi.detach(), delta.detach(), g, ref, o)
+    assert np.abs(dd - ref).max() < 1e-12 * np.abs(ref).max()
+    assert rc.grad.item() == pytest.approx(drc, rel=1e-12)
+    v = torch.from_numpy(inputs.white_noise(n, 603)).to(dev)
+    with torch.no_grad():
+        lp = (g * Fn.apply(delta + 1e-4 * v, rc, ctx, a, om, float(n), o)).sum().item()
+        lm = (g * Fn.apply(delta - 1e-4 * v, rc, ctx, a, om, float(n), o)).sum().item()
+    assert float((delta.grad * v).sum()) == pytest.approx((lp - lm) / 2e-4, rel=1e-5)
