@@ -187,6 +187,25 @@ __device__ __forceinline__ void gather2(Nb<T> &v, Nb<T> &w, const T *__restrict_
     v.ymzp = __ldg(S + r0m + mp); w.ymzp = __ldg(BS + r0m + mp);
 }
 
+// square root and quotient in the kernel's precision: IEEE in FP64; in FP32
+// the PTX approximate forms (sqrt.approx, div.approx: a few ulp), since every
+// FP32 result feeds a correction that the FP64 defect of the mixed solve
+// re-measures
+__device__ __forceinline__ double k_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ double k_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float k_sqrt(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float k_div(float a, float b)
+{
+    float r;
+    asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
 template <typename T>
 __device__ __forceinline__ T ipow(T x, int p)
 {
@@ -225,7 +244,7 @@ __device__ __forceinline__ T op_N(const OpK<T> &op, const LevK<T> &L, const Nb<T
         // (~1e-16 alpha) is far below the residuals the solve resolves; FP32
         // keeps the rationalised form, which does not cancel for Sigma << alpha^2
         if (sizeof(T) == 8) return T(0.75) * op.sgn_alpha * (sqrt(arg) - op.abs_alpha);
-        return T(2) * op.sgn_alpha * sig / (op.abs_alpha + sqrt(arg));
+        return k_div(T(2) * op.sgn_alpha * sig, op.abs_alpha + k_sqrt(arg));
     } else {
         const T dx = v.xp - v.xm, dy = v.yp - v.ym, dz = v.zp - v.zm;
         const T dx2 = dx * dx, dy2 = dy * dy, dz2 = dz * dz;
@@ -234,7 +253,7 @@ __device__ __forceinline__ T op_N(const OpK<T> &op, const LevK<T> &L, const Nb<T
                    + (Cxy * dx * dy + Cxz * dx * dz + Cyz * dy * dz) * L.to;
         const T pw2 = ipow(G2, op.nkmo - 2);
         const T sigma1 = op.k1 + op.k2 * pw2 * G2;
-        return (s - op.k3 * pw2 * Tt) / sigma1;
+        return k_div(s - op.k3 * pw2 * Tt, sigma1);
     }
 }
 
@@ -255,7 +274,7 @@ __device__ __forceinline__ T nd_clamped(const OpK<T> &op, T sig)
 {
     const T arg = op.alpha2 + op.c83 * sig;
     if (arg < T(0)) return T(-0.75) * op.alpha;
-    return T(2) * op.sgn_alpha * sig / (op.abs_alpha + sqrt(arg));
+    return k_div(T(2) * op.sgn_alpha * sig, op.abs_alpha + k_sqrt(arg));
 }
 
 template <typename T>
@@ -282,8 +301,8 @@ __device__ __forceinline__ T op_dN(const OpK<T> &op, const LevK<T> &L, const Nb<
             clamp = 1;
             return nd_clamped(op, sig1) - nd_clamped(op, sig0);
         }
-        const T den = sqrt(arg0) + sqrt(arg1);
-        return den > T(0) ? T(2) * op.sgn_alpha * dQ / den : T(0);
+        const T den = k_sqrt(arg0) + k_sqrt(arg1);
+        return den > T(0) ? k_div(T(2) * op.sgn_alpha * dQ, den) : T(0);
     } else {
         const T edx = v.xp - v.xm, edy = v.yp - v.ym, edz = v.zp - v.zm;
         const T bdx = w.xp - w.xm, bdy = w.yp - w.ym, bdz = w.zp - w.zm;
@@ -323,8 +342,8 @@ __device__ __forceinline__ T op_dN(const OpK<T> &op, const LevK<T> &L, const Nb<
         const T pw0 = ipow(G20, nk - 2), pw1 = ipow(G21, nk - 2);
         const T dP = pw1 * dT + T0 * dG2 * g_nm2;
         const T B0 = op.k1 + op.k2 * pw0 * G20, B1 = op.k1 + op.k2 * pw1 * G21;
-        const T N0 = (s - op.k3 * pw0 * T0) / B0;
-        return (-op.k3 * dP - N0 * op.k2 * dG2 * g_nm1) / B1;
+        const T N0 = k_div(s - op.k3 * pw0 * T0, B0);
+        return k_div(-op.k3 * dP - N0 * op.k2 * dG2 * g_nm1, B1);
     }
 }
 

@@ -92,11 +92,52 @@ k_smooth2(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un
     smooth_pair<T, CORR>(*opp, L, Uc, Uo, Un, Sc, Fc, smooth_cf<T>(sc), colour, Bc, Bo, i, j, 2 * mp2);
 }
 
+// four cells of an FP32 colour row per thread (rows whose length is a
+// multiple of 4, colour arrays below 2^31 elements)
+template <bool CORR>
+__global__ void __launch_bounds__(256)
+k_smooth4(const float *__restrict__ Uc, const float *__restrict__ Uo, float *__restrict__ Un,
+          const float *__restrict__ Sc, const float *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<float> L,
+          const OpK<float> *__restrict__ opp, int colour, const float *__restrict__ Bc, const float *__restrict__ Bo)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = blockIdx.z;
+    if (4 * q >= L.half || j >= L.n) return;
+    smooth_quad<CORR>(*opp, L, Uc, Uo, Un, Sc, Fc, smooth_cf<float>(sc), colour, Bc, Bo, i, j, 4 * q);
+}
+
+template <typename T>
+bool launch_smooth4(const LevArrays<T> &, const LevK<T> &, const OpK<T> *, int, int, cudaStream_t)
+{
+    return false;
+}
+
+template <>
+bool launch_smooth4<float>(const LevArrays<float> &L, const LevK<float> &K, const OpK<float> *op, int colour, int nb,
+                           cudaStream_t st)
+{
+    if (L.half % 4 != 0 || L.ncol >= (1LL << 31)) return false;
+    const dim3 b = block_mj(L.half / 4);
+    const dim3 g = grid_mj(L.half / 4, L.n, b, L.n);
+    if (L.base[0])
+        k_smooth4<true><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], L.f[colour],
+                                         L.sc, K, op, colour, L.base[colour], L.base[1 - colour]);
+    else
+        k_smooth4<false><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], L.f[colour],
+                                          L.sc, K, op, colour, nullptr, nullptr);
+    return true;
+}
+
 template <typename T>
 void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, int colour, cudaStream_t st)
 {
     const int nb = 1 - L.cur[colour];
     const LevK<T> K = make_levk<T>(L.n, L.h);
+    if (launch_smooth4<T>(L, K, op, colour, nb, st)) {
+        Lw->cur[colour] = nb;
+        return;
+    }
     if (L.half % 2 == 0) {
         const dim3 b = block_mj(L.half / 2);
         const dim3 g = grid_mj(L.half / 2, L.n, b, L.n);
