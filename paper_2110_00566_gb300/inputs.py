@@ -114,18 +114,24 @@ def _kgrid(n, box):
     return k[:, None, None], k[None, :, None], kz[None, None, :]
 
 
-def linear_field_k(n, box, pk, seed, noise=None):
-    """Fourier modes (numpy rfftn convention) of a Gaussian field with
-    spectrum pk on an n^3 lattice of side box: FFT(white noise) *
-    sqrt(P(k) / V_cell); the k = 0 mode is zero."""
-    w = white_noise(n, seed) if noise is None else np.asarray(noise, dtype=np.float64)
-    wk = np.fft.rfftn(w)
+def pk_amplitude(n, box, pk):
+    """sqrt(P(|k|) / V_cell) on the rfftn grid (n, n, n/2 + 1) of an n^3
+    lattice of side box, zero at k = 0: the factor that turns the FFT of
+    unit white noise into a field with spectrum pk."""
     kx, ky, kz = _kgrid(n, box)
     kk = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
     kk[0, 0, 0] = 1.0
     amp = np.sqrt(pk(kk) / (box / n) ** 3)
     amp[0, 0, 0] = 0.0
-    return wk * amp
+    return np.ascontiguousarray(amp)
+
+
+def linear_field_k(n, box, pk, seed, noise=None):
+    """Fourier modes (numpy rfftn convention) of a Gaussian field with
+    spectrum pk on an n^3 lattice of side box: FFT(white noise) *
+    sqrt(P(k) / V_cell); the k = 0 mode is zero."""
+    w = white_noise(n, seed) if noise is None else np.asarray(noise, dtype=np.float64)
+    return np.fft.rfftn(w) * pk_amplitude(n, box, pk)
 
 
 def linear_field(n, box, pk, seed):
