@@ -60,6 +60,10 @@ def args():
     p.add_argument("--inner", type=int, default=0, help="FP32 cycles per FP64 defect (0: library default)")
     p.add_argument("--batch", type=int, default=64, help="instances of the batched form (0: skip)")
     p.add_argument("--adj-ng", type=int, default=128, help="mesh of the adjoint form (0: skip)")
+    p.add_argument("--pm-adj-ng", type=int, default=128,
+                   help="mesh (= particles per side) of the differentiable PM run (0: skip)")
+    p.add_argument("--pm-adj-steps", type=int, default=20)
+    p.add_argument("--fd-dirs", type=int, default=16, help="finite-difference directions for the PM gradient")
     return p.parse_args()
 
 
@@ -382,6 +386,58 @@ def main():
         return {"ng": n, "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
                 "adjoint_cycles": cyc, "precision": "fp64"}
 
+    def adjoint_pm():
+        """The differentiable PM run of the adjoint workload: n^3 particles
+        on an n^3 mesh, L = 2n Mpc/h, a.pm_adj_steps leapfrog steps from
+        z = 10 to 0 with the nDGP solve (FP64) at every step, loss = MSE of
+        the 32-bin P(k) against the spectrum of the run from another seed,
+        gradients with respect to the white noise and R_c (checkpoints every
+        4 steps).  Reports forward and forward+reverse times and the
+        gradient against central differences along random unit directions."""
+        import numpy as np
+        from paper_2110_00566_gb300 import inputs
+        n, box, a0 = a.pm_adj_ng, 2.0 * a.pm_adj_ng, 1.0 / 11.0
+        D = inputs.growth_lcdm(a0, 0.3)
+        E0 = float(np.sqrt(0.3 / a0 ** 3 + 0.7))
+        cfg = B.make_dpm_config(n, box, 0.3, a0, 1.0, a.pm_adj_steps, 4, 32, 1, D,
+                                a0 * a0 * E0 * D * inputs.growth_rate_lcdm(a0, 0.3))
+        amp = torch.from_numpy(inputs.pk_amplitude(n, box, inputs.pk_cutoff())).to(dev)
+        w = torch.from_numpy(inputs.white_noise(n, 5).astype(np.float32).astype(np.float64)).to(dev)
+        w6 = torch.from_numpy(inputs.white_noise(n, 6).astype(np.float32).astype(np.float64)).to(dev)
+        o = B.opts(rtol=1e-10, max_cycles=60)
+        tgt, _, _, _ = B.dpm_run(ctx, cfg, amp, w6, a.rc, o=o)
+        grad = torch.empty_like(w)
+        B.dpm_run(ctx, cfg, amp, w, a.rc, tgt, grad, o=o)      # warm-up (workspace, plans)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, L0, _, stf = B.dpm_run(ctx, cfg, amp, w, a.rc, tgt, o=o)
+        t1 = time.perf_counter()
+        _, _, drc, stb = B.dpm_run(ctx, cfg, amp, w, a.rc, tgt, grad, o=o)
+        t2 = time.perf_counter()
+        fwd, both = (t1 - t0) * 1e3, (t2 - t1) * 1e3
+        g = grad.cpu().numpy()
+        errs = []
+        eps = 1e-3
+        for q in range(a.fd_dirs):
+            v = inputs.white_noise(n, 700 + q)
+            v /= np.linalg.norm(v)
+            vt = torch.from_numpy(v).to(dev)
+            lp = B.dpm_run(ctx, cfg, amp, w + eps * vt, a.rc, tgt, o=o)[1]
+            lm = B.dpm_run(ctx, cfg, amp, w - eps * vt, a.rc, tgt, o=o)[1]
+            fd = (lp - lm) / (2 * eps)
+            ad = float(np.sum(g * v))
+            errs.append(abs(ad - fd) / max(abs(fd), 1e-300))
+        hr = 1e-4 * a.rc
+        fdr = (B.dpm_run(ctx, cfg, amp, w, a.rc + hr, tgt, o=o)[1] - B.dpm_run(ctx, cfg, amp, w, a.rc - hr, tgt, o=o)[1]) / (2 * hr)
+        return {"ng": n, "particles": n ** 3, "box_mpch": box, "steps": a.pm_adj_steps, "checkpoint_every": 4,
+                "nbins": 32, "loss": L0, "forward_ms": fwd, "forward_and_reverse_ms": both,
+                "reverse_over_forward": (both - fwd) / fwd, "solver_cycles_forward": stf.cycles,
+                "solver_cycles_forward_and_reverse": stb.cycles,
+                "fd_directions": a.fd_dirs, "fd_max_rel_err_noise": max(errs) if errs else None,
+                "fd_median_rel_err_noise": float(np.median(errs)) if errs else None,
+                "dL_dRc": drc, "fd_rel_err_Rc": abs(drc - fdr) / max(abs(fdr), 1e-300),
+                "precision": "fp64 particles and solves"}
+
     primary = timed(a.precision)
     second = None
     if not a.no_forms:
@@ -389,6 +445,7 @@ def main():
     e2e_primary = None if a.no_e2e else e2e(primary)
     batch_form = batched() if (a.batch > 0 and not a.no_forms) else None
     adj_form = adjoint() if (a.adj_ng > 0 and not a.no_forms) else None
+    pm_adj_form = adjoint_pm() if (a.pm_adj_ng > 0 and not a.no_forms) else None
 
     if rank != 0:
         if dist:
@@ -412,6 +469,8 @@ def main():
         forms["batched"] = batch_form
     if adj_form is not None:
         forms["adjoint"] = adj_form
+    if pm_adj_form is not None:
+        forms["adjoint_pm"] = pm_adj_form
     cb = None if a.no_cpu else cpu_baseline(delta.cpu().numpy(), a)
     line = {"metric": METRIC, "value": primary["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": primary["ms_per_step"], "higher_is_better": True,

@@ -120,11 +120,13 @@ typedef struct {
     int warm_start;       /* 1: phi holds the initial guess; 0: start at 0    */
     int coarse_sweeps;    /* red-black sweeps on the coarsest level           */
     int use_graph;        /* 1: replay each cycle from a captured CUDA graph  */
-    int inner_cycles;     /* MIXED: FP32 cycles per FP64 defect correction    */
+    int inner_cycles;     /* MIXED: FP32 cycles per FP64 defect correction;
+                             0: chosen per correction from the observed
+                             convergence rate (1..5)                         */
 } mg_opts;
 
 /* pre = post = 2, max_cycles = 30, V, FP64, rtol = 1e-8, atol = 0,
- * warm_start = 0, coarse_sweeps = 64, use_graph = 1, inner_cycles = 2. */
+ * warm_start = 0, coarse_sweeps = 64, use_graph = 1, inner_cycles = 0. */
 void mg_opts_default(mg_opts *o);
 
 typedef struct {
@@ -285,6 +287,80 @@ int mg_solve_adjoint(mg_ctx *ctx, const mg_grid *g, const mg_dgp_params *p,
                      const mg_opts *opts, const double *phi, const double *delta,
                      const double *dL_dphi, double *dL_ddelta_out,
                      double *dL_drc_out, mg_stats *stats);
+
+/* ---- differentiable particle-mesh run ------------------------------------
+ * The forward model (Sec. 3.1 and 3.1.1 with the nDGP field of Sec. 3.2.3)
+ * and its hand-written reverse pass, in FP64 particle state:
+ *   white noise w (ng^3) -> linear density delta_L(k) = amp(k) FFT(w)(k)
+ *   -> Zel'dovich displacement psi(k) = i k delta_L(k) / k^2 in mesh cells
+ *   (the Nyquist component of k dropped) -> one particle per cell on the
+ *   lattice (i + 1/2, j + 1/2, k + 1/2): x = lattice + growth psi wrapped
+ *   into [0, ng), p = vel psi;
+ *   nsteps kick-drift-kick steps of constant da from a_start to a_end, the
+ *   first with a half kick, each: delta = CIC(x) (mean removed), Phi_N by
+ *   the 7-point Green's function, phi by mg_solve_dgp (model 1, warm
+ *   started from the previous step), Phi = Phi_N + phi/2, force -grad Phi by
+ *   central differences at the 8 CIC cells interpolated with the CIC
+ *   weights, p += F da_k/(a E(a)), x += p da/(a_m^3 E(a_m)), wrap;
+ *   P_b = <|FFT(CIC(x_T))|^2> L^3/ng^6 over the modes of bin b,
+ *   b = floor((|m| - 1) nbins / (ng/2 - 1)) for integer wavevectors
+ *   1 <= |m| <= ng/2 (|m| = ng/2 in the last bin), and the loss
+ *   L = mean_b (P_b - target_b)^2.
+ * amp is given on the rfft grid (ng, ng, ng/2+1): sqrt(P(k) / V_cell).
+ * Particle arrays are (np, 3) FP64 in lattice order; meshes ng^3 FP64.
+ * Arrays may be host or device pointers (copied in and out as needed)
+ * unless marked HOST.  Errors: MG_ERR_ARG, MG_ERR_CUDA, MG_ERR_OOM, and the
+ * solves' codes. */
+typedef struct {
+    int ng;                /* mesh cells per side = particles per side       */
+    double box_mpch;       /* L                                              */
+    double omega_m;
+    double a_start, a_end; /* the run's scale factors                        */
+    int nsteps;            /* leapfrog steps (>= 1)                          */
+    int checkpoint_every;  /* steps between stored states for the reverse
+                              pass (>= 1): memory ~ nsteps/checkpoint_every
+                              particle states + checkpoint_every meshes     */
+    int nbins;             /* P(k) bins (>= 1)                               */
+    int model;             /* 0 GR, 1 nDGP                                   */
+    double growth;         /* D(a_start): displacement factor of the ICs     */
+    double vel;            /* momentum factor of the ICs, a^2 E D f          */
+} dpm_config;
+
+/* Runs the model from noise; writes P (HOST, nbins) and, with target_pk
+ * (HOST, nbins) given, the loss (HOST scalar).  With dL_dnoise_out given,
+ * also runs the reverse pass (needs target_pk): dL/dw (ng^3) and, when
+ * dL_drc_out (HOST) is given, dL/dR_c.  stats (or NULL): the last forward
+ * nDGP solve; stats->cycles holds the total number of solver cycles. */
+int dpm_run(mg_ctx *ctx, const dpm_config *cfg, const mg_opts *opts, const double *amp,
+            const double *noise, double rc_h0, const double *target_pk, double *pk_out,
+            double *loss_out, double *dL_dnoise_out, double *dL_drc_out, mg_stats *stats);
+
+/* The pieces, each with its adjoint (vector-Jacobian product), for
+ * checking.  dpm_ic: positions and momenta from noise; dpm_ic_adjoint:
+ * dL/dw from dL/dx and dL/dp. */
+int dpm_ic(mg_ctx *ctx, const dpm_config *cfg, const double *amp, const double *noise,
+           double *pos_out, double *mom_out);
+int dpm_ic_adjoint(mg_ctx *ctx, const dpm_config *cfg, const double *amp, const double *dpos,
+                   const double *dmom, double *dnoise_out);
+/* delta = (ng^3/np) sum of CIC weights - 1, mean removed; the weights are
+ * summed in 64-bit fixed point (2^-40), so the result is deterministic.
+ * The adjoint writes dL/dx = sum over the 8 cells of dW/dx (ng^3/np) dL/ddelta. */
+int dpm_deposit(mg_ctx *ctx, int ng, const double *pos, long long np, double *delta_out);
+int dpm_deposit_adjoint(mg_ctx *ctx, int ng, const double *pos, long long np, const double *ddelta,
+                        double *dpos_out);
+/* F = CIC interpolation of -grad (Phi_N + phi/2) (phi may be NULL); the
+ * adjoint writes dL/dx (the interpolation weights' part) and dL/dPhi_N
+ * (dL/dphi is half of it). */
+int dpm_force(mg_ctx *ctx, int ng, const double *phin, const double *phi, const double *pos,
+              long long np, double *force_out);
+int dpm_force_adjoint(mg_ctx *ctx, int ng, const double *phin, const double *phi, const double *pos,
+                      long long np, const double *dforce, double *dpos_out, double *dphin_out);
+/* P_b (HOST, nbins) and the bins' full-grid mode counts (HOST, or NULL);
+ * the adjoint writes dL/ddelta for dL/dP (HOST, nbins). */
+int dpm_power_spectrum(mg_ctx *ctx, int ng, double box_mpch, int nbins, const double *delta,
+                       double *pk_out, double *counts_out);
+int dpm_power_spectrum_adjoint(mg_ctx *ctx, int ng, double box_mpch, int nbins, const double *delta,
+                               const double *dpk, double *ddelta_out);
 
 /* ---- kernel-level entry points (one multigrid step each) ---------------
  * For checking each kernel against a reference implementation.  Natural

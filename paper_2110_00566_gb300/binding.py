@@ -68,6 +68,12 @@ class pm_state(C.Structure):
                 ("model", C.c_int), ("first", C.c_int), ("dgp", mg_dgp_params), ("phi_ws", C.c_void_p)]
 
 
+class dpm_config(C.Structure):
+    _fields_ = [("ng", C.c_int), ("box_mpch", C.c_double), ("omega_m", C.c_double), ("a_start", C.c_double),
+                ("a_end", C.c_double), ("nsteps", C.c_int), ("checkpoint_every", C.c_int), ("nbins", C.c_int),
+                ("model", C.c_int), ("growth", C.c_double), ("vel", C.c_double)]
+
+
 class mg_op_params(C.Structure):
     _fields_ = [("model", C.c_int), ("alpha", C.c_double), ("nkmo", C.c_int), ("gamma", C.c_double),
                 ("bterm", C.c_double)]
@@ -97,6 +103,16 @@ def _declare(L):
         "pm_newton_potential": (C.c_int, [_VP, C.c_int, C.c_double, C.c_double, _VP, _VP]),
         "mg_solve_adjoint": (C.c_int, [_VP, _P(mg_grid), _P(mg_dgp_params), _P(mg_opts), _VP, _VP, _VP, _VP,
                                        _VP, _P(mg_stats)]),
+        "dpm_run": (C.c_int, [_VP, _P(dpm_config), _P(mg_opts), _VP, _VP, C.c_double, _VP, _VP, _VP, _VP, _VP,
+                              _P(mg_stats)]),
+        "dpm_ic": (C.c_int, [_VP, _P(dpm_config), _VP, _VP, _VP, _VP]),
+        "dpm_ic_adjoint": (C.c_int, [_VP, _P(dpm_config), _VP, _VP, _VP, _VP]),
+        "dpm_deposit": (C.c_int, [_VP, C.c_int, _VP, C.c_longlong, _VP]),
+        "dpm_deposit_adjoint": (C.c_int, [_VP, C.c_int, _VP, C.c_longlong, _VP, _VP]),
+        "dpm_force": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, C.c_longlong, _VP]),
+        "dpm_force_adjoint": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, C.c_longlong, _VP, _VP, _VP]),
+        "dpm_power_spectrum": (C.c_int, [_VP, C.c_int, C.c_double, C.c_int, _VP, _VP, _VP]),
+        "dpm_power_spectrum_adjoint": (C.c_int, [_VP, C.c_int, C.c_double, C.c_int, _VP, _VP, _VP]),
         "mg_op_smooth": (C.c_int, [_VP, _P(mg_op_params), C.c_int, C.c_int, C.c_double, _VP, _VP, _VP,
                                    C.c_double, C.c_int, _VP]),
         "mg_op_smooth_corr": (C.c_int, [_VP, _P(mg_op_params), C.c_int, C.c_double, _VP, _VP, _VP, _VP,
@@ -300,6 +316,96 @@ def mg_solve_adjoint(ctx: Context, ng, box_mpch, a, omega_m, rc_h0, phi, delta, 
                                 C.byref(st))
     ctx._rc(rc)
     return rc, drc.value, st
+
+
+# ------------------------------------------------- differentiable PM run
+
+def make_dpm_config(ng, box_mpch, omega_m, a_start, a_end, nsteps, checkpoint_every=4, nbins=32, model=1,
+                    growth=1.0, vel=0.0) -> dpm_config:
+    return dpm_config(int(ng), float(box_mpch), float(omega_m), float(a_start), float(a_end), int(nsteps),
+                      int(checkpoint_every), int(nbins), int(model), float(growth), float(vel))
+
+
+def _host_f64(x, n):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1))
+    if a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+def dpm_run(ctx: Context, cfg: dpm_config, amp, noise, rc_h0, target=None, dnoise_out=None, want_drc=True,
+            o: mg_opts = None):
+    """Forward run (and the reverse pass when dnoise_out is given).
+    Returns (P (nbins,), loss or None, dL/dR_c or None, stats)."""
+    _check_dtype(amp, "f64")
+    _check_dtype(noise, "f64")
+    _check_dtype(dnoise_out, "f64")
+    pk = np.zeros(cfg.nbins)
+    tgt = None if target is None else _host_f64(target, cfg.nbins)
+    loss = C.c_double(0.0)
+    drc = C.c_double(0.0)
+    st = mg_stats()
+    rc = lib().dpm_run(ctx.h, C.byref(cfg), C.byref(o or opts()), _ptr(amp), _ptr(noise), float(rc_h0),
+                       None if tgt is None else tgt.ctypes.data, pk.ctypes.data,
+                       None if tgt is None else C.cast(C.pointer(loss), C.c_void_p), _ptr(dnoise_out),
+                       C.cast(C.pointer(drc), C.c_void_p) if (dnoise_out is not None and want_drc) else None,
+                       C.byref(st))
+    ctx._rc(rc)
+    return (pk, None if tgt is None else loss.value,
+            drc.value if (dnoise_out is not None and want_drc) else None, st)
+
+
+def dpm_ic(ctx: Context, cfg: dpm_config, amp, noise, pos_out, mom_out):
+    for x in (amp, noise, pos_out, mom_out):
+        _check_dtype(x, "f64")
+    ctx._rc(lib().dpm_ic(ctx.h, C.byref(cfg), _ptr(amp), _ptr(noise), _ptr(pos_out), _ptr(mom_out)))
+
+
+def dpm_ic_adjoint(ctx: Context, cfg: dpm_config, amp, dpos, dmom, dnoise_out):
+    for x in (amp, dpos, dmom, dnoise_out):
+        _check_dtype(x, "f64")
+    ctx._rc(lib().dpm_ic_adjoint(ctx.h, C.byref(cfg), _ptr(amp), _ptr(dpos), _ptr(dmom), _ptr(dnoise_out)))
+
+
+def dpm_deposit(ctx: Context, ng, pos, delta_out):
+    _check_dtype(pos, "f64")
+    _check_dtype(delta_out, "f64")
+    ctx._rc(lib().dpm_deposit(ctx.h, int(ng), _ptr(pos), pos.shape[0], _ptr(delta_out)))
+
+
+def dpm_deposit_adjoint(ctx: Context, ng, pos, ddelta, dpos_out):
+    for x in (pos, ddelta, dpos_out):
+        _check_dtype(x, "f64")
+    ctx._rc(lib().dpm_deposit_adjoint(ctx.h, int(ng), _ptr(pos), pos.shape[0], _ptr(ddelta), _ptr(dpos_out)))
+
+
+def dpm_force(ctx: Context, ng, phin, phi, pos, force_out):
+    for x in (phin, phi, pos, force_out):
+        _check_dtype(x, "f64")
+    ctx._rc(lib().dpm_force(ctx.h, int(ng), _ptr(phin), _ptr(phi), _ptr(pos), pos.shape[0], _ptr(force_out)))
+
+
+def dpm_force_adjoint(ctx: Context, ng, phin, phi, pos, dforce, dpos_out, dphin_out):
+    for x in (phin, phi, pos, dforce, dpos_out, dphin_out):
+        _check_dtype(x, "f64")
+    ctx._rc(lib().dpm_force_adjoint(ctx.h, int(ng), _ptr(phin), _ptr(phi), _ptr(pos), pos.shape[0],
+                                    _ptr(dforce), _ptr(dpos_out), _ptr(dphin_out)))
+
+
+def dpm_power_spectrum(ctx: Context, ng, box_mpch, nbins, delta):
+    _check_dtype(delta, "f64")
+    pk, cnt = np.zeros(nbins), np.zeros(nbins)
+    ctx._rc(lib().dpm_power_spectrum(ctx.h, int(ng), float(box_mpch), int(nbins), _ptr(delta), pk.ctypes.data,
+                                     cnt.ctypes.data))
+    return pk, cnt
+
+
+def dpm_power_spectrum_adjoint(ctx: Context, ng, box_mpch, nbins, delta, dpk, ddelta_out):
+    _check_dtype(delta, "f64")
+    _check_dtype(ddelta_out, "f64")
+    d = _host_f64(dpk, nbins)
+    ctx._rc(lib().dpm_power_spectrum_adjoint(ctx.h, int(ng), float(box_mpch), int(nbins), _ptr(delta),
+                                             d.ctypes.data, _ptr(ddelta_out)))
 
 
 # ---------------------------------------------------------------- kernel level

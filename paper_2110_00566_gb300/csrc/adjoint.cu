@@ -352,6 +352,104 @@ void adj_release(mg_ctx *ctx)
     }
 }
 
+// the adjoint solve on device arrays (validated arguments): dL/ddelta into
+// dout, dL/dR_c into *drc; CUDA failures throw CudaFail
+int adjoint_dev(mg_ctx *ctx, int n, double a, double om, double Rc, const mg_opts &o, const double *dphi,
+                const double *ddel, const double *dg, double *dout, double *drc, mg_stats *st)
+{
+    mg_stats loc{};
+    cudaStream_t s = ctx->stream;
+    const long long cnt = (long long)n * n * n;
+    const size_t b = sizeof(double) * (size_t)cnt;
+    // workspace (one per context, reallocated when the size changes)
+    AdjWork *w = (AdjWork *)ctx->adj;
+    if (w && w->n0 != n) {
+        MG_CK(cudaStreamSynchronize(s));
+        adj_free(w);
+        w = nullptr;
+        ctx->adj = nullptr;
+    }
+    if (!w) {
+        w = adj_alloc(ctx, n);
+        ctx->adj = w;
+    }
+    // background scalars (Eq. beta_dgp) and their R_c derivatives
+    const double oma = om / (a * a * a), ol = 1.0 - om;
+    const double B0 = (oma + 2.0 * ol) / std::sqrt(oma + ol);   // beta = 1 + Rc B0
+    const double beta = 1.0 + Rc * B0, beta_p = B0;
+    const double alpha = 3.0 * beta * a * a / (Rc * Rc);
+    const double alpha_p = 3.0 * a * a * (beta_p / (Rc * Rc) - 2.0 * beta / (Rc * Rc * Rc));
+    const double ks = (alpha / beta) * om / a;
+    const double ks_p = ((alpha_p * beta - alpha * beta_p) / (beta * beta)) * om / a;
+    double *dscr = w->scal;
+    // level 0: phi, s = ks (delta - <delta>), rhs = Pi g
+    AdjLev &A0 = w->L[0];
+    MG_CK(cudaMemcpyAsync(A0.phi, dphi, b, cudaMemcpyDeviceToDevice, s));
+    k_mean_into<<<g1(cnt), 256, 0, s>>>(ddel, cnt, dscr + 4, w->rb);
+    MG_CK(cudaMemsetAsync(A0.s, 0, b, s));
+    k_axpy_nat<<<g1(cnt), 256, 0, s>>>(A0.s, ddel, 0.0, ks, cnt, dscr + 4);
+    k_mean_into<<<g1(cnt), 256, 0, s>>>(dg, cnt, dscr + 5, w->rb);
+    MG_CK(cudaMemsetAsync(A0.rhs, 0, b, s));
+    k_axpy_nat<<<g1(cnt), 256, 0, s>>>(A0.rhs, dg, 0.0, 1.0, cnt, dscr + 5);
+    for (size_t l = 0; l < w->L.size(); ++l) {
+        AdjLev &L = w->L[l];
+        const long long c = (long long)L.n * L.n * L.n;
+        if (l > 0) {
+            k_restrict_nat<<<g1(c), 256, 0, s>>>(w->L[l - 1].phi, w->L[l - 1].n, L.phi);
+            k_restrict_nat<<<g1(c), 256, 0, s>>>(w->L[l - 1].s, w->L[l - 1].n, L.s);
+        }
+        k_adj_coef<<<g1(c), 256, 0, s>>>(L.phi, L.s, L.n, L.h, alpha, L.K[0], L.K[1], L.K[2], L.K[3], L.K[4],
+                                         L.K[5], L.Np, L.dNa);
+        k_adj_v<<<g1(c), 256, 0, s>>>(L);
+    }
+    MG_CK(cudaMemsetAsync(A0.lam[A0.cur], 0, b, s));
+    MG_CK(cudaMemsetAsync(dscr + 8, 0, sizeof(double) * 32, s));
+    // reference norm: rms(Pi g)
+    k_adj_resid<<<g1(cnt), 256, 0, s>>>(A0, A0.lam[A0.cur], nullptr, A0.res, w->rb, dscr);
+    double h3[3];
+    MG_CK(cudaMemcpyAsync(h3, dscr, sizeof h3, cudaMemcpyDeviceToHost, s));
+    MG_CK(cudaStreamSynchronize(s));
+    const double ref = std::sqrt(h3[0] / (double)cnt);
+    loc.eps_ref = ref;
+    loc.eps[0] = ref;
+    loc.n_eps = 1;
+    int cyc = 0;
+    bool conv = ref <= o.atol || ref == 0.0;
+    while (!conv && cyc < o.max_cycles) {
+        adj_vcycle(ctx, *w, 0, o);
+        ++cyc;
+        k_mean_into<<<g1(cnt), 256, 0, s>>>(A0.lam[A0.cur], cnt, dscr + 8, w->rb);
+        k_adj_resid<<<g1(cnt), 256, 0, s>>>(A0, A0.lam[A0.cur], dscr + 8, A0.res, w->rb, dscr);
+        MG_CK(cudaMemcpyAsync(h3, dscr, sizeof h3, cudaMemcpyDeviceToHost, s));
+        MG_CK(cudaStreamSynchronize(s));
+        const double eps = std::sqrt(h3[0] / (double)cnt);
+        if (loc.n_eps < 65) loc.eps[loc.n_eps++] = eps;
+        if (!std::isfinite(eps)) {
+            if (st) *st = loc;
+            return set_err(ctx, MG_ERR_NONFINITE, "adjoint: non-finite residual");
+        }
+        conv = eps <= o.rtol * ref + o.atol;
+    }
+    // gradients
+    double hmean[2];
+    MG_CK(cudaMemcpyAsync(hmean, dscr + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MG_CK(cudaStreamSynchronize(s));
+    k_mean_into<<<g1(cnt), 256, 0, s>>>(A0.lam[A0.cur], cnt, dscr + 8, w->rb);
+    k_adj_grad<<<g1(cnt), 256, 0, s>>>(A0.lam[A0.cur], A0.Np, A0.dNa, ddel, dscr + 8, cnt, hmean[0], ks, alpha_p,
+                                       ks_p, dout, w->rb, dscr + 6);
+    k_mean_into<<<g1(cnt), 256, 0, s>>>(dout, cnt, dscr + 7, w->rb);
+    k_axpy_nat<<<g1(cnt), 256, 0, s>>>(dout, dout, 0.0, 1.0, cnt, dscr + 7);
+    double hdr = 0.0;
+    MG_CK(cudaMemcpyAsync(&hdr, dscr + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MG_CK(cudaStreamSynchronize(s));
+    if (drc) *drc = hdr;
+    loc.cycles = cyc;
+    const int rc = conv ? MG_OK : MG_WARN_NOT_CONVERGED;
+    loc.status = rc;
+    if (st) *st = loc;
+    return rc;
+}
+
 }  // namespace mg
 
 using namespace mg;
@@ -374,102 +472,18 @@ extern "C" int mg_solve_adjoint(mg_ctx *ctx, const mg_grid *g, const mg_dgp_para
     mg_stats loc{};
     try {
         enter(ctx);
-        cudaStream_t s = ctx->stream;
         const int n = g->ng;
-        const long long cnt = (long long)n * n * n;
-        const size_t b = sizeof(double) * (size_t)cnt;
+        const size_t b = sizeof(double) * (size_t)n * n * n;
         const double *dphi = (const double *)stage_in(ctx, 0, phi, b, true);
         const double *ddel = (const double *)stage_in(ctx, 1, delta, b, true);
         const double *dg = (const double *)stage_in(ctx, 2, dL_dphi, b, true);
         double *dout = (double *)stage_in(ctx, 3, dL_ddelta_out, b, false);
-        // workspace (one per context, reallocated when the size changes)
-        AdjWork *w = (AdjWork *)ctx->adj;
-        if (w && w->n0 != n) {
-            MG_CK(cudaStreamSynchronize(s));
-            adj_free(w);
-            w = nullptr;
-            ctx->adj = nullptr;
-        }
-        if (!w) {
-            w = adj_alloc(ctx, n);
-            ctx->adj = w;
-        }
-        // background scalars (Eq. beta_dgp) and their R_c derivatives
-        const double a = g->a, om = g->omega_m, Rc = p->rc_h0;
-        const double oma = om / (a * a * a), ol = 1.0 - om;
-        const double B0 = (oma + 2.0 * ol) / std::sqrt(oma + ol);   // beta = 1 + Rc B0
-        const double beta = 1.0 + Rc * B0, beta_p = B0;
-        const double alpha = 3.0 * beta * a * a / (Rc * Rc);
-        const double alpha_p = 3.0 * a * a * (beta_p / (Rc * Rc) - 2.0 * beta / (Rc * Rc * Rc));
-        const double ks = (alpha / beta) * om / a;
-        const double ks_p = ((alpha_p * beta - alpha * beta_p) / (beta * beta)) * om / a;
-        double *dscr = w->scal;
-        // level 0: phi, s = ks (delta - <delta>), rhs = Pi g
-        AdjLev &A0 = w->L[0];
-        MG_CK(cudaMemcpyAsync(A0.phi, dphi, b, cudaMemcpyDeviceToDevice, s));
-        k_mean_into<<<g1(cnt), 256, 0, s>>>(ddel, cnt, dscr + 4, w->rb);
-        MG_CK(cudaMemsetAsync(A0.s, 0, b, s));
-        k_axpy_nat<<<g1(cnt), 256, 0, s>>>(A0.s, ddel, 0.0, ks, cnt, dscr + 4);
-        k_mean_into<<<g1(cnt), 256, 0, s>>>(dg, cnt, dscr + 5, w->rb);
-        MG_CK(cudaMemsetAsync(A0.rhs, 0, b, s));
-        k_axpy_nat<<<g1(cnt), 256, 0, s>>>(A0.rhs, dg, 0.0, 1.0, cnt, dscr + 5);
-        for (size_t l = 0; l < w->L.size(); ++l) {
-            AdjLev &L = w->L[l];
-            const long long c = (long long)L.n * L.n * L.n;
-            if (l > 0) {
-                k_restrict_nat<<<g1(c), 256, 0, s>>>(w->L[l - 1].phi, w->L[l - 1].n, L.phi);
-                k_restrict_nat<<<g1(c), 256, 0, s>>>(w->L[l - 1].s, w->L[l - 1].n, L.s);
-            }
-            k_adj_coef<<<g1(c), 256, 0, s>>>(L.phi, L.s, L.n, L.h, alpha, L.K[0], L.K[1], L.K[2], L.K[3], L.K[4],
-                                             L.K[5], L.Np, L.dNa);
-            k_adj_v<<<g1(c), 256, 0, s>>>(L);
-        }
-        MG_CK(cudaMemsetAsync(A0.lam[A0.cur], 0, b, s));
-        MG_CK(cudaMemsetAsync(dscr + 8, 0, sizeof(double) * 32, s));
-        // reference norm: rms(Pi g)
-        k_adj_resid<<<g1(cnt), 256, 0, s>>>(A0, A0.lam[A0.cur], nullptr, A0.res, w->rb, dscr);
-        double h3[3];
-        MG_CK(cudaMemcpyAsync(h3, dscr, sizeof h3, cudaMemcpyDeviceToHost, s));
-        MG_CK(cudaStreamSynchronize(s));
-        const double ref = std::sqrt(h3[0] / (double)cnt);
-        loc.eps_ref = ref;
-        loc.eps[0] = ref;
-        loc.n_eps = 1;
-        int cyc = 0;
-        bool conv = ref <= o.atol || ref == 0.0;
-        while (!conv && cyc < o.max_cycles) {
-            adj_vcycle(ctx, *w, 0, o);
-            ++cyc;
-            k_mean_into<<<g1(cnt), 256, 0, s>>>(A0.lam[A0.cur], cnt, dscr + 8, w->rb);
-            k_adj_resid<<<g1(cnt), 256, 0, s>>>(A0, A0.lam[A0.cur], dscr + 8, A0.res, w->rb, dscr);
-            MG_CK(cudaMemcpyAsync(h3, dscr, sizeof h3, cudaMemcpyDeviceToHost, s));
-            MG_CK(cudaStreamSynchronize(s));
-            const double eps = std::sqrt(h3[0] / (double)cnt);
-            if (loc.n_eps < 65) loc.eps[loc.n_eps++] = eps;
-            if (!std::isfinite(eps)) {
-                leave(ctx);
-                if (stats) *stats = loc;
-                return set_err(ctx, MG_ERR_NONFINITE, "adjoint: non-finite residual");
-            }
-            conv = eps <= o.rtol * ref + o.atol;
-        }
-        // gradients
-        double hmean[2];
-        MG_CK(cudaMemcpyAsync(hmean, dscr + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
-        MG_CK(cudaStreamSynchronize(s));
-        k_mean_into<<<g1(cnt), 256, 0, s>>>(A0.lam[A0.cur], cnt, dscr + 8, w->rb);
-        k_adj_grad<<<g1(cnt), 256, 0, s>>>(A0.lam[A0.cur], A0.Np, A0.dNa, ddel, dscr + 8, cnt, hmean[0], ks, alpha_p,
-                                           ks_p, dout, w->rb, dscr + 6);
-        k_mean_into<<<g1(cnt), 256, 0, s>>>(dout, cnt, dscr + 7, w->rb);
-        k_axpy_nat<<<g1(cnt), 256, 0, s>>>(dout, dout, 0.0, 1.0, cnt, dscr + 7);
         double hdr = 0.0;
-        MG_CK(cudaMemcpyAsync(&hdr, dscr + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
-        MG_CK(cudaStreamSynchronize(s));
-        stage_out(ctx, dL_ddelta_out, dout, b);
-        if (dL_drc_out) *dL_drc_out = hdr;
-        loc.cycles = cyc;
-        rc = conv ? MG_OK : MG_WARN_NOT_CONVERGED;
-        loc.status = rc;
+        rc = adjoint_dev(ctx, n, g->a, g->omega_m, p->rc_h0, o, dphi, ddel, dg, dout, &hdr, &loc);
+        if (rc >= 0) {
+            stage_out(ctx, dL_ddelta_out, dout, b);
+            if (dL_drc_out) *dL_drc_out = hdr;
+        }
         leave(ctx);
     } catch (CudaFail &f) {
         return f.code;

@@ -610,7 +610,7 @@ int solve_batch(mg_ctx *ctx, int count, const mg_instance *inst, const mg_opts &
     }
     MG_CK(cudaMemcpyAsync(w->d_prog, prog.data(), sizeof(Phase) * prog.size(), cudaMemcpyHostToDevice, s));
     MG_CK(cudaMemcpyAsync(w->d_inst, hI.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, s));
-    BatchArgs A{w->d_inst, count, w->d_prog, (int)prog.size(), std::max(1, o.inner_cycles), o.max_cycles,
+    BatchArgs A{w->d_inst, count, w->d_prog, (int)prog.size(), o.inner_cycles > 0 ? o.inner_cycles : 4, o.max_cycles,
                 o.coarse_sweeps};
     int dev = 0, sms = 0, per_sm = 0;
     MG_CK(cudaGetDevice(&dev));

@@ -80,6 +80,7 @@ struct Pyramid {
 
 struct PmWork;     // particle-mesh workspace (pm.cu)
 struct BatchWork;  // batched-ensemble workspace (batch.cu)
+struct DpmWork;    // differentiable particle-mesh workspace (dpm.cu)
 
 struct ModelDesc {
     int model;         // 0 nDGP, 1 Kmouflage
@@ -113,6 +114,7 @@ struct mg_ctx {
     mg::PmWork *pm = nullptr;
     mg::BatchWork *batch = nullptr;
     void *adj = nullptr;             // adjoint workspace (adjoint.cu)
+    mg::DpmWork *dpm = nullptr;      // differentiable PM workspace (dpm.cu)
     size_t batch_partial_cap = 0;    // reduction tiles per instance
     std::map<int, int> tuned_tx;     // autotuned tile width per level size
     // profiling of the finest-level smoother (events recorded in the graphs)
@@ -152,5 +154,14 @@ int solve_dgp_dev(mg_ctx *ctx, int n, double a, double om, double rc, const doub
                   const mg_opts &o, mg_stats *st);
 void cic_deposit_dev(mg_ctx *ctx, int ng, const float *pos, long long np, double *delta);
 int check_opts(mg_ctx *ctx, const mg_opts &o);
+
+// FFT workspace of the particle-mesh step for an n^3 mesh, and the
+// Newtonian potential Lap Phi = (3/2) Omega_m a^-1 delta on device arrays
+void pm_fft_setup(mg_ctx *ctx, int n);
+void newton_potential_dev(mg_ctx *ctx, int n, double a, double om, const double *delta, double *out);
+// the nDGP adjoint solve on device arrays (validated arguments)
+int adjoint_dev(mg_ctx *ctx, int n, double a, double om, double Rc, const mg_opts &o, const double *dphi,
+                const double *ddel, const double *dg, double *dout, double *drc, mg_stats *st);
+void dpm_release(mg_ctx *ctx);
 
 }  // namespace mg

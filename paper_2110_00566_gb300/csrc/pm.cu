@@ -204,7 +204,7 @@ static void pm_release_fft(PmWork &w)
     w.fft_n = 0;
 }
 
-static void pm_fft_setup(mg_ctx *ctx, int n)
+void pm_fft_setup(mg_ctx *ctx, int n)
 {
     PmWork &w = pmw(ctx);
     if (w.fft_n == n) return;
@@ -228,7 +228,7 @@ static void pm_fft_setup(mg_ctx *ctx, int n)
 
 // Lap Phi = (3/2) Omega_m a^-1 delta (Eq. GR_poisson_codeunit), solved with
 // the 7-point Green's function by FFT (Sec. 3.1); the zero mode is dropped.
-static void newton_potential_dev(mg_ctx *ctx, int n, double a, double om, const double *delta, double *out)
+void newton_potential_dev(mg_ctx *ctx, int n, double a, double om, const double *delta, double *out)
 {
     PmWork &w = pmw(ctx);
     const double scale = 1.5 * om / a / ((double)n * n * n);

@@ -492,7 +492,13 @@ int solve_mixed(mg_ctx *ctx, int n, const ModelDesc &md, const double *delta, do
         if (st) *st = loc;
         return set_err(ctx, MG_ERR_NONFINITE, "non-finite initial residual (delta has NaN/Inf?)");
     }
-    const int inner = std::max(1, o.inner_cycles);
+    // inner FP32 cycles per FP64 defect: fixed, or (inner_cycles = 0) as
+    // many as the observed per-cycle reduction rho needs to reach the
+    // tolerance, 1..MAX_ADAPT_INNER (rho = 0.1 assumed before the first
+    // measurement); the FP32 correction resolves about 1e-6 of itself, so
+    // longer inner runs gain nothing
+    constexpr int MAX_ADAPT_INNER = 5;
+    double rho = 0.1;
     const long long per_cycle = cycle_updates(P32, o, 0, o.cycle);
     const long long per_launch = cycle_launches(P32, o, 0, o.cycle) + 1;
     long long launches = 6 + (P32.nlev - 1) + (o.warm_start ? 1 : 0);
@@ -506,7 +512,15 @@ int solve_mixed(mg_ctx *ctx, int n, const ModelDesc &md, const double *delta, do
         launch_set_corr_scalars(P32.scal, s0, P32.nlev, s);
         MG_CK(cudaMemsetAsync(E0.U(0), 0, sizeof(float) * E0.ncol, s));
         MG_CK(cudaMemsetAsync(E0.U(1), 0, sizeof(float) * E0.ncol, s));
-        for (int k = 0; k < inner && cyc < o.max_cycles; ++k) {
+        int inner = o.inner_cycles;
+        if (inner <= 0) {
+            const double target = o.rtol * eps_ref + o.atol;
+            const double need = (eps > target && target > 0) ? std::log(target / eps) / std::log(rho) : 1.0;
+            inner = (int)std::min<double>(MAX_ADAPT_INNER, std::max(1.0, std::ceil(need - 1e-9)));
+        }
+        const double eps_before = eps;
+        int ran = 0;
+        for (int k = 0; k < inner && cyc < o.max_cycles; ++k, ++ran) {
             cycle_and_norm(ctx, P32, o, false);
             ++cyc;
             launches += per_launch - 1;
@@ -530,6 +544,8 @@ int solve_mixed(mg_ctx *ctx, int n, const ModelDesc &md, const double *delta, do
             return set_err(ctx, MG_ERR_NONFINITE, "non-finite residual after correction %d", outer);
         }
         conv = eps <= o.rtol * eps_ref + o.atol;
+        if (ran > 0 && eps > 0 && eps < eps_before)
+            rho = std::min(0.9, std::max(1e-3, std::pow(eps / eps_before, 1.0 / ran)));
     }
     const double c_final = h.c, clamps = h.clamps;
     launch_mean_split<double>(Uu, U64.ncol, &s0->mean, P64.rb, s);
@@ -620,7 +636,7 @@ void mg_opts_default(mg_opts *o)
     o->warm_start = 0;
     o->coarse_sweeps = 64;
     o->use_graph = 1;
-    o->inner_cycles = 2;
+    o->inner_cycles = 0;
 }
 
 int mg_ctx_create(mg_ctx **out, int device, void *cuda_stream)
@@ -666,6 +682,7 @@ void mg_ctx_destroy(mg_ctx *ctx)
     for (auto &p : ctx->p32c) release_pyramid(p.second);
     batch_free(ctx);
     adj_release(ctx);
+    dpm_release(ctx);
     mg_pm_free(ctx);
     for (int q = 0; q < mg_ctx::NSTAGE; ++q)
         if (ctx->stage[q]) cudaFree(ctx->stage[q]);

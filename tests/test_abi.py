@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def header_functions():
     src = open(os.path.join(ROOT, "include", "mgglam.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*[A-Za-z_][\w \*]*?\b((?:mg|pm)_\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*[A-Za-z_][\w \*]*?\b((?:mg|pm|dpm)_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
