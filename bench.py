@@ -285,7 +285,7 @@ def main():
             gbs = alg / (ms * 1e-3) / 1e9
             tf = FLOPS_PER_CELL_FP64 * (ng ** 3 / 2) / (ms * 1e-3) / 1e12
             return {"bound": "alu", "achieved": tf, "peak": fp64_tf, "unit": "TFLOP/s", "frac": tf / fp64_tf,
-                    "traffic": None, "kernel": "k_smooth<double> finest half-sweep",
+                    "traffic": None, "kernel": "k_smooth2<double> finest half-sweep",
                     "peak_source": "FP64 FMA rate measured by mg_probe_alu_peaks on this GPU",
                     "alg_flops_per_cell": FLOPS_PER_CELL_FP64, "avg_launch_ms": ms, "launches": r["fine_launches"],
                     "hbm_view": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
@@ -296,7 +296,7 @@ def main():
         alg = 14 * ng ** 3
         gbs = alg / (ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                "traffic": None, "kernel": "k_smooth<float, correction> finest half-sweep",
+                "traffic": None, "kernel": "k_smooth4<float, correction, nDGP> finest half-sweep",
                 "peak_source": peak_src, "avg_launch_ms": ms, "launches": r["fine_launches"],
                 "alg_bytes_per_launch": alg}
 
@@ -386,6 +386,47 @@ def main():
         return {"ng": n, "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
                 "adjoint_cycles": cyc, "precision": "fp64"}
 
+    def kmouflage():
+        """Kmouflage solves on the headline mesh with a 512 Mpc/h box (the
+        same Zel'dovich load, seed 3): (n, K0) = (2, 1) and (3, 1),
+        beta = 0.2, a = 1, lambda^2 = 3 (1 - Omega_m), phibar'/H0 = -1e-3,
+        A = exp(-0.02); the FP64 solve and the mixed-precision solve, the
+        latter's phi against the former's (both to rtol)."""
+        import numpy as np
+        from paper_2110_00566_gb300 import inputs
+        box = 2.0 * a.box
+        pk = inputs.pk_cutoff(0.96, 5.0, 0.8)
+        p_, _ = inputs.zeldovich(a.np, ng, box, pk, 1.0, seed=3)
+        dk = torch.empty((ng, ng, ng), dtype=torch.float64, device=dev)
+        B.pm_cic_deposit(ctx, ng, torch.from_numpy(p_).to(dev), dk)
+        lam = float(np.sqrt(3.0 * 0.7))
+        out = {}
+        for nk, k0 in ((2, 1.0), (3, 1.0)):
+            res = {}
+            phis = {}
+            for prec in ("fp64", "mixed"):
+                o = B.opts(rtol=a.rtol, max_cycles=60,
+                           precision=B.MG_PREC_FP64 if prec == "fp64" else B.MG_PREC_MIXED)
+                phi = torch.zeros_like(dk)
+                B.mg_solve_kmouflage(ctx, ng, box, 1.0, 0.3, nk, k0, 0.2, lam, -1e-3, float(np.exp(-0.02)), dk, phi, o)
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                _, st = B.mg_solve_kmouflage(ctx, ng, box, 1.0, 0.3, nk, k0, 0.2, lam, -1e-3, float(np.exp(-0.02)),
+                                             dk, phi, o)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                ms = e0.elapsed_time(e1)
+                res[prec] = {"ms": ms, "cycles": st.cycles, "value": st.cell_updates / (ms * 1e-3) / 1e9,
+                             "final_eps_over_eps_ref": st.eps[st.n_eps - 1] / st.eps_ref}
+                phis[prec] = phi
+            l2 = float(torch.linalg.vector_norm(phis["mixed"] - phis["fp64"]) / torch.linalg.vector_norm(phis["fp64"]))
+            out["n%d_K0_%g" % (nk, k0)] = {"fp64": res["fp64"], "mixed": res["mixed"],
+                                          "mixed_speedup": res["fp64"]["ms"] / res["mixed"]["ms"],
+                                          "phi_rel_l2_mixed_vs_fp64": l2, "unit": UNIT}
+        out["config"] = "512^3 mesh, L = %g Mpc/h, beta = 0.2, a = 1" % box
+        return out
+
     def adjoint_pm():
         """The differentiable PM run of the adjoint workload: n^3 particles
         on an n^3 mesh, L = 2n Mpc/h, a.pm_adj_steps leapfrog steps from
@@ -446,6 +487,7 @@ def main():
     batch_form = batched() if (a.batch > 0 and not a.no_forms) else None
     adj_form = adjoint() if (a.adj_ng > 0 and not a.no_forms) else None
     pm_adj_form = adjoint_pm() if (a.pm_adj_ng > 0 and not a.no_forms) else None
+    kmo_form = kmouflage() if not a.no_forms else None
 
     if rank != 0:
         if dist:
@@ -471,6 +513,8 @@ def main():
         forms["adjoint"] = adj_form
     if pm_adj_form is not None:
         forms["adjoint_pm"] = pm_adj_form
+    if kmo_form is not None:
+        forms["kmouflage"] = kmo_form
     cb = None if a.no_cpu else cpu_baseline(delta.cpu().numpy(), a)
     line = {"metric": METRIC, "value": primary["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": primary["ms_per_step"], "higher_is_better": True,

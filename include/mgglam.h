@@ -122,7 +122,7 @@ typedef struct {
     int use_graph;        /* 1: replay each cycle from a captured CUDA graph  */
     int inner_cycles;     /* MIXED: FP32 cycles per FP64 defect correction;
                              0: chosen per correction from the observed
-                             convergence rate (1..5)                         */
+                             convergence rate (1..4)                         */
 } mg_opts;
 
 /* pre = post = 2, max_cycles = 30, V, FP64, rtol = 1e-8, atol = 0,

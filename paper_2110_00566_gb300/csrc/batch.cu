@@ -86,6 +86,11 @@ __device__ __forceinline__ int mj_tiles(const BLev &L, int planes)
     return cdiv(L.half, L.tx) * cdiv(L.n, ty) * planes;
 }
 
+// tiles of 256 quads (four cells of a colour row per thread) over a level
+// whose rows are a multiple of 4 long
+__device__ __forceinline__ bool quad_level(const BLev &L) { return (L.half & 3) == 0; }
+__device__ __forceinline__ int quad_tiles(const BLev &L) { return cdiv(L.n * L.n * (L.half / 4), BTHREADS); }
+
 // tiles over the coarse cells (K, J) of plane I of the level below l
 __device__ __forceinline__ int coarse_tiles(const BLev &L)
 {
@@ -243,19 +248,33 @@ __global__ void __launch_bounds__(BTHREADS, 2) k_batch(BatchArgs A)
         }
         if (P.type == PH_SMOOTH) {
             const int c = P.colour;
-            const int total = prefix([&](int q) { return d < A.inst[q].nlev - 1 ? mj_tiles(A.inst[q].lev[d], A.inst[q].lev[d].n) : 0; });
+            const int total = prefix([&](int q) {
+                const BLev &L = A.inst[q].lev[d];
+                return d < A.inst[q].nlev - 1 ? (quad_level(L) ? quad_tiles(L) : mj_tiles(L, L.n)) : 0;
+            });
             for (int t = blockIdx.x; t < total; t += gridDim.x) {
                 const int q = find_inst(pref, count, t);
                 const BInst &I = A.inst[q];
                 const BLev &L = I.lev[d];
+                const LevK<float> K = make_levk<float>(L.n, L.h);
+                if (quad_level(L)) {
+                    // flat quad index: row (i, j), quad m0 / 4 fastest
+                    const int qr = L.half / 4;
+                    const int Q = (t - pref[q]) * BTHREADS + (int)threadIdx.x;
+                    if (Q < L.n * L.n * qr) {
+                        const int m0 = 4 * (Q % qr), r = Q / qr;
+                        smooth_quad<true, 0>(I.opf, K, L.u[P.cur[c]][c], L.u[P.cur[1 - c]][1 - c],
+                                             L.u[1 - P.cur[c]][c], L.s[c], L.f[c], L.sc->cf32, c, L.base[c],
+                                             L.base[1 - c], r / L.n, r % L.n, m0);
+                    }
+                    continue;
+                }
                 const int gx = cdiv(L.half, L.tx), gy = cdiv(L.n, BTHREADS / L.tx);
                 int m, j, i;
                 tile_xyz(t - pref[q], gx, gy, L.tx, m, j, i);
-                if (m < L.half && j < L.n) {
-                    const LevK<float> K = make_levk<float>(L.n, L.h);
+                if (m < L.half && j < L.n)
                     smooth_cell<float, true>(I.opf, K, L.u[P.cur[c]][c], L.u[P.cur[1 - c]][1 - c], L.u[1 - P.cur[c]][c],
                                              L.s[c], L.f[c], L.sc->cf32, c, L.base[c], L.base[1 - c], i, j, m);
-                }
             }
             return;
         }

@@ -224,14 +224,16 @@ __device__ __forceinline__ T ipow(T x, int p)
 //  sqrt argument gives -(3/4) alpha and is counted.
 //  Kmouflage (Sec. 3.2.4, Eq. kmf_eqn_codeunit_final / c~):
 //    N = (s - 2(n-1) gamma (G^2)^(n-2) T) / (1 + gamma b^(n-1) + (2n+1)gamma/3 (G^2)^(n-1))
-template <typename T>
+// MODEL: 0 or 1 compiles only that operator (the caller knows the model);
+// -1 dispatches on op.model at run time
+template <typename T, int MODEL = -1>
 __device__ __forceinline__ T op_N(const OpK<T> &op, const LevK<T> &L, const Nb<T> &v, T s, int &clamp)
 {
     const T Sx = v.xp + v.xm, Sy = v.yp + v.ym, Sz = v.zp + v.zm;
     const T Cxy = (v.xpyp + v.xmym) - (v.xpym + v.xmyp);
     const T Cxz = (v.xpzp + v.xmzm) - (v.xpzm + v.xmzp);
     const T Cyz = (v.ypzp + v.ymzm) - (v.ypzm + v.ymzp);
-    if (op.model == 0) {
+    if (MODEL == 0 || (MODEL < 0 && op.model == 0)) {
         const T a = Sx - Sy, b = Sx - Sz, c = Sy - Sz;
         const T Q = (a * a + b * b + c * c) * L.qd + (Cxy * Cxy + Cxz * Cxz + Cyz * Cyz) * L.qo;
         const T sig = Q + s;
@@ -277,7 +279,7 @@ __device__ __forceinline__ T nd_clamped(const OpK<T> &op, T sig)
     return k_div(T(2) * op.sgn_alpha * sig, op.abs_alpha + k_sqrt(arg));
 }
 
-template <typename T>
+template <typename T, int MODEL = -1>
 __device__ __forceinline__ T op_dN(const OpK<T> &op, const LevK<T> &L, const Nb<T> &v, const Nb<T> &w, T s,
                                    int &clamp)
 {
@@ -289,7 +291,7 @@ __device__ __forceinline__ T op_dN(const OpK<T> &op, const LevK<T> &L, const Nb<
     const T bCxy = (w.xpyp + w.xmym) - (w.xpym + w.xmyp);
     const T bCxz = (w.xpzp + w.xmzm) - (w.xpzm + w.xmzp);
     const T bCyz = (w.ypzp + w.ymzm) - (w.ypzm + w.ymzp);
-    if (op.model == 0) {
+    if (MODEL == 0 || (MODEL < 0 && op.model == 0)) {
         const T ea = eSx - eSy, eb = eSx - eSz, ec = eSy - eSz;
         const T ba = bSx - bSy, bb = bSx - bSz, bc = bSy - bSz;
         const T dQ = (ea * (T(2) * ba + ea) + eb * (T(2) * bb + eb) + ec * (T(2) * bc + ec)) * L.qd +

@@ -32,10 +32,11 @@ struct CudaFail {
 struct CycleKey {
     std::vector<int> state;  // cur[] of every level before the cycle
     int pre, post, cycle, coarse_sweeps, nlev, prof, norm;
+    int model;               // the kernels are specialised on the operator
     bool operator<(const CycleKey &o) const
     {
-        return std::tie(state, pre, post, cycle, coarse_sweeps, nlev, prof, norm) <
-               std::tie(o.state, o.pre, o.post, o.cycle, o.coarse_sweeps, o.nlev, o.prof, o.norm);
+        return std::tie(state, pre, post, cycle, coarse_sweeps, nlev, prof, norm, model) <
+               std::tie(o.state, o.pre, o.post, o.cycle, o.coarse_sweeps, o.nlev, o.prof, o.norm, o.model);
     }
 };
 

@@ -94,7 +94,7 @@ k_smooth2(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un
 
 // four cells of an FP32 colour row per thread (rows whose length is a
 // multiple of 4, colour arrays below 2^31 elements)
-template <bool CORR>
+template <bool CORR, int MODEL>
 __global__ void __launch_bounds__(256)
 k_smooth4(const float *__restrict__ Uc, const float *__restrict__ Uo, float *__restrict__ Un,
           const float *__restrict__ Sc, const float *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<float> L,
@@ -104,7 +104,7 @@ k_smooth4(const float *__restrict__ Uc, const float *__restrict__ Uo, float *__r
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int i = blockIdx.z;
     if (4 * q >= L.half || j >= L.n) return;
-    smooth_quad<CORR>(*opp, L, Uc, Uo, Un, Sc, Fc, smooth_cf<float>(sc), colour, Bc, Bo, i, j, 4 * q);
+    smooth_quad<CORR, MODEL>(*opp, L, Uc, Uo, Un, Sc, Fc, smooth_cf<float>(sc), colour, Bc, Bo, i, j, 4 * q);
 }
 
 template <typename T>
@@ -120,12 +120,21 @@ bool launch_smooth4<float>(const LevArrays<float> &L, const LevK<float> &K, cons
     if (L.half % 4 != 0 || L.ncol >= (1LL << 31)) return false;
     const dim3 b = block_mj(L.half / 4);
     const dim3 g = grid_mj(L.half / 4, L.n, b, L.n);
-    if (L.base[0])
-        k_smooth4<true><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], L.f[colour],
-                                         L.sc, K, op, colour, L.base[colour], L.base[1 - colour]);
-    else
-        k_smooth4<false><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], L.f[colour],
-                                          L.sc, K, op, colour, nullptr, nullptr);
+    const float *U0 = L.U(colour), *U1 = L.U(1 - colour);
+    float *Un = L.u[nb][colour];
+#define MG_SMOOTH4(CORR, MODEL)                                                                              \
+    k_smooth4<CORR, MODEL><<<g, b, 0, st>>>(U0, U1, Un, L.s[colour], L.f[colour], L.sc, K, op, colour,      \
+                                            CORR ? L.base[colour] : nullptr, CORR ? L.base[1 - colour] : nullptr)
+    if (L.base[0]) {
+        if (L.model == 0) MG_SMOOTH4(true, 0);
+        else if (L.model == 1) MG_SMOOTH4(true, 1);
+        else MG_SMOOTH4(true, -1);
+    } else {
+        if (L.model == 0) MG_SMOOTH4(false, 0);
+        else if (L.model == 1) MG_SMOOTH4(false, 1);
+        else MG_SMOOTH4(false, -1);
+    }
+#undef MG_SMOOTH4
     return true;
 }
 

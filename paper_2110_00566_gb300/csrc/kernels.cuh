@@ -22,10 +22,12 @@ struct LevArrays {
     T *ur[2];            // R u saved for the correction
     T *base[2];          // correction form: base field (nullptr: plain form)
     LevScal *sc;         // this level's device scalars
+    int model = -1;      // operator of the uploaded OpK (0 nDGP, 1 Kmouflage), -1 unknown
     T *U(int colour) const { return u[cur[colour]][colour]; }
 };
 
 template <typename T> OpK<T> make_opk(int model, double alpha, int nkmo, double gamma, double bterm);
+
 
 template <typename T>
 void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, int colour, cudaStream_t st);

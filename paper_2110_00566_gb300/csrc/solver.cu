@@ -321,7 +321,7 @@ static void cycle_and_norm(mg_ctx *ctx, Pyramid<T> &P, const mg_opts &o, bool no
         record();
         return;
     }
-    CycleKey key{P.state(), o.pre, o.post, o.cycle, o.coarse_sweeps, P.nlev, ctx->prof_on, norm ? 1 : 0};
+    CycleKey key{P.state(), o.pre, o.post, o.cycle, o.coarse_sweeps, P.nlev, ctx->prof_on, norm ? 1 : 0, P.L[0].model};
     auto it = P.graphs.find(key);
     if (it == P.graphs.end()) {
         const std::vector<int> pre_state = P.state();
@@ -359,6 +359,7 @@ static void upload_op(mg_ctx *ctx, Pyramid<T> &P, const ModelDesc &md)
     MG_CK(cudaMemcpyAsync(P.opT, &hT, sizeof hT, cudaMemcpyHostToDevice, ctx->stream));
     MG_CK(cudaMemcpyAsync(P.opD, &hD, sizeof hD, cudaMemcpyHostToDevice, ctx->stream));
     MG_CK(cudaStreamSynchronize(ctx->stream));
+    for (auto &L : P.L) L.model = md.model;
 }
 
 // Plain solve: every level in the storage precision T (FP64 for the
@@ -497,7 +498,7 @@ int solve_mixed(mg_ctx *ctx, int n, const ModelDesc &md, const double *delta, do
     // tolerance, 1..MAX_ADAPT_INNER (rho = 0.1 assumed before the first
     // measurement); the FP32 correction resolves about 1e-6 of itself, so
     // longer inner runs gain nothing
-    constexpr int MAX_ADAPT_INNER = 5;
+    constexpr int MAX_ADAPT_INNER = 4;
     double rho = 0.1;
     const long long per_cycle = cycle_updates(P32, o, 0, o.cycle);
     const long long per_launch = cycle_launches(P32, o, 0, o.cycle) + 1;

@@ -27,7 +27,7 @@ def lap6(e):
 
 
 @pytest.mark.parametrize("name", list(MODELS))
-@pytest.mark.parametrize("n,h", [(16, 1.0), (24, 2.0)])
+@pytest.mark.parametrize("n,h", [(16, 1.0), (24, 2.0), (128, 1.0), (256, 2.0)])
 def test_correction_smoother(B, ctx, name, n, h):
     """A correction 1e-4 the size of the base field: a naive FP32
     N(b+e) - N(b) would lose ~3 digits; the expanded form keeps FP32
