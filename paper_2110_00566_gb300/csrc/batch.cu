@@ -279,28 +279,43 @@ __global__ void __launch_bounds__(BTHREADS, 2) k_batch(BatchArgs A)
             return;
         }
         if (P.type == PH_RR) {
-            const int total = prefix([&](int q) { return d < A.inst[q].nlev - 1 ? coarse_tiles(A.inst[q].lev[d]) : 0; });
+            auto rr_tiles = [&](const BLev &L) {
+                const int nc = L.n / 2;
+                return (nc & 3) == 0 ? cdiv(nc * nc * (nc / 4), BTHREADS) : coarse_tiles(L);
+            };
+            const int total = prefix([&](int q) { return d < A.inst[q].nlev - 1 ? rr_tiles(A.inst[q].lev[d]) : 0; });
             for (int t = blockIdx.x; t < total; t += gridDim.x) {
                 const int q = find_inst(pref, count, t);
                 BInst &I = A.inst[q];
                 const BLev &L = I.lev[d];
                 const BLev &C = I.lev[d + 1];
                 const int nc = L.n / 2;
-                const int gx = cdiv(nc, L.tx), gy = cdiv(nc, BTHREADS / L.tx);
                 const int lt = t - pref[q];
-                int K, J, Ii;
-                tile_xyz(lt, gx, gy, L.tx, K, J, Ii);
                 const double c_old = L.sc->c;
                 const double cshift = c_old - L.sc->fshift;
                 double acc[4] = {0.0, 0.0, 0.0, 0.0};
-                if (K < nc && J < nc) {
-                    const LevK<float> Kf = make_levk<float>(L.n, L.h);
-                    rr_cell<float, true>(I.opf, Kf, L.u[P.cur[0]][0], L.u[P.cur[1]][1], L.s[0], L.s[1], L.f[0], L.f[1],
-                                         L.base[0], L.base[1], cshift, C.u[P.curc[0]][0], C.u[P.curc[1]][1], C.ur[0],
-                                         C.ur[1], C.f[0], C.f[1], Ii, J, K, acc);
+                const LevK<float> Kf = make_levk<float>(L.n, L.h);
+                if ((nc & 3) == 0) {
+                    // flat index over (I, J, K0 / 4), four coarse cells per thread
+                    const int qr = nc / 4;
+                    const int Q = lt * BTHREADS + (int)threadIdx.x;
+                    if (Q < nc * nc * qr) {
+                        const int K0 = 4 * (Q % qr), r = Q / qr;
+                        rr_quad<true, 0>(I.opf, Kf, L.u[P.cur[0]][0], L.u[P.cur[1]][1], L.s[0], L.s[1], L.f[0],
+                                         L.f[1], L.base[0], L.base[1], cshift, C.u[P.curc[0]][0], C.u[P.curc[1]][1],
+                                         C.ur[0], C.ur[1], C.f[0], C.f[1], r / nc, r % nc, K0, acc);
+                    }
+                } else {
+                    const int gx = cdiv(nc, L.tx), gy = cdiv(nc, BTHREADS / L.tx);
+                    int K, J, Ii;
+                    tile_xyz(lt, gx, gy, L.tx, K, J, Ii);
+                    if (K < nc && J < nc)
+                        rr_cell<float, true>(I.opf, Kf, L.u[P.cur[0]][0], L.u[P.cur[1]][1], L.s[0], L.s[1], L.f[0],
+                                             L.f[1], L.base[0], L.base[1], cshift, C.u[P.curc[0]][0],
+                                             C.u[P.curc[1]][1], C.ur[0], C.ur[1], C.f[0], C.f[1], Ii, J, K, acc);
                 }
                 double tot[4];
-                if (tile_sum<4>(acc, I.partials, I.counter, lt, coarse_tiles(L), tot) && threadIdx.x == 0) {
+                if (tile_sum<4>(acc, I.partials, I.counter, lt, rr_tiles(L), tot) && threadIdx.x == 0) {
                     const double cnt = (double)L.n * L.n * L.n;
                     const double c_new = tot[0] / cnt;
                     set_c(L.sc, c_new);

@@ -95,8 +95,7 @@ k_smooth2(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un
 // four cells of an FP32 colour row per thread (rows whose length is a
 // multiple of 4, colour arrays below 2^31 elements)
 template <bool CORR, int MODEL>
-__global__ void __launch_bounds__(256)
-k_smooth4(const float *__restrict__ Uc, const float *__restrict__ Uo, float *__restrict__ Un,
+__global__ void __launch_bounds__(256) k_smooth4(const float *__restrict__ Uc, const float *__restrict__ Uo, float *__restrict__ Un,
           const float *__restrict__ Sc, const float *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<float> L,
           const OpK<float> *__restrict__ opp, int colour, const float *__restrict__ Bc, const float *__restrict__ Bo)
 {
@@ -270,10 +269,70 @@ k_resid_restrict(const T *__restrict__ U0, const T *__restrict__ U1, const T *__
         finish_resid(sc, tot, (double)L.n * L.n * L.n, c_old);
 }
 
+// four coarse cells per thread (FP32, coarse rows a multiple of 4 long)
+template <bool CORR, int MODEL>
+__global__ void __launch_bounds__(256, 2) k_resid_restrict4(const float *__restrict__ U0, const float *__restrict__ U1, const float *__restrict__ S0,
+                  const float *__restrict__ S1, const float *__restrict__ F0, const float *__restrict__ F1,
+                  LevScal *sc, RedBuf rb, LevK<float> L, const OpK<float> *__restrict__ opp, float *__restrict__ Uc0,
+                  float *__restrict__ Uc1, float *__restrict__ URc0, float *__restrict__ URc1,
+                  float *__restrict__ RDc0, float *__restrict__ RDc1, const float *__restrict__ B0,
+                  const float *__restrict__ B1)
+{
+    const OpK<float> op = *opp;
+    const int nc = L.n / 2;
+    const int K4 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const double c_old = sc->c;
+    const double cshift = c_old - sc->fshift;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (4 * K4 < nc && J < nc)
+        for (int I = blockIdx.z; I < nc; I += gridDim.z)
+            rr_quad<CORR, MODEL>(op, L, U0, U1, S0, S1, F0, F1, B0, B1, cshift, Uc0, Uc1, URc0, URc1, RDc0, RDc1, I,
+                                 J, 4 * K4, acc);
+    double tot[4];
+    if (grid_sum<4>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0)
+        finish_resid(sc, tot, (double)L.n * L.n * L.n, c_old);
+}
+
+template <typename T>
+bool launch_resid_restrict4(const LevArrays<T> &, LevArrays<T> &, const OpK<T> *, const RedBuf &, cudaStream_t)
+{
+    return false;
+}
+
+template <>
+bool launch_resid_restrict4<float>(const LevArrays<float> &Lf, LevArrays<float> &Lc, const OpK<float> *op,
+                                   const RedBuf &rb, cudaStream_t st)
+{
+    const int nc = Lf.n / 2;
+    if (nc % 4 != 0 || Lf.ncol >= (1LL << 31)) return false;
+    const dim3 b = block_mj(nc / 4);
+    dim3 g = grid_mj(nc / 4, nc, b, 1);
+    g.z = red_z(g, nc, rb.cap);
+    const LevK<float> K = make_levk<float>(Lf.n, Lf.h);
+#define MG_RR4(CORR, MODEL)                                                                                       \
+    k_resid_restrict4<CORR, MODEL><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb, \
+                                                    K, op, Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], Lc.fbuf[0],      \
+                                                    Lc.fbuf[1], CORR ? Lf.base[0] : nullptr,                      \
+                                                    CORR ? Lf.base[1] : nullptr)
+    if (Lf.base[0]) {
+        if (Lf.model == 0) MG_RR4(true, 0);
+        else if (Lf.model == 1) MG_RR4(true, 1);
+        else MG_RR4(true, -1);
+    } else {
+        if (Lf.model == 0) MG_RR4(false, 0);
+        else if (Lf.model == 1) MG_RR4(false, 1);
+        else MG_RR4(false, -1);
+    }
+#undef MG_RR4
+    return true;
+}
+
 template <typename T>
 void launch_resid_restrict(const LevArrays<T> &Lf, LevArrays<T> &Lc, const OpK<T> *op, const RedBuf &rb,
                            cudaStream_t st)
 {
+    if (launch_resid_restrict4<T>(Lf, Lc, op, rb, st)) return;
     const int nc = Lf.n / 2;
     const dim3 b = block_mj(nc);
     dim3 g = grid_mj(nc, nc, b, 1);
