@@ -505,6 +505,7 @@ def main():
                        "speedup_vs_primary": primary["ms_per_step"] / second["ms_per_step"],
                        "phi_rel_l2_vs_primary": l2, "cycles_per_solve": st1.cycles,
                        "final_eps_over_eps_ref": st1.eps[st1.n_eps - 1] / st1.eps_ref,
+                       "eps_measured_over_eps_ref": [st1.eps[q] / st1.eps_ref for q in range(st1.n_eps)],
                        "gpu_launches": second["launches"], "clocks": second["clocks"],
                        "roofline": roofline(second, name, fp64_tf)}
     if batch_form is not None:
@@ -523,6 +524,7 @@ def main():
             "config": {"workload": workload_name(a), "precision": a.precision, "cycles_per_solve": st0.cycles,
                        "cell_updates_per_solve": st0.cell_updates,
                        "final_eps_over_eps_ref": st0.eps[st0.n_eps - 1] / st0.eps_ref,
+                       "eps_measured_over_eps_ref": [st0.eps[q] / st0.eps_ref for q in range(st0.n_eps)],
                        "l2": "inputs larger than L2 (delta %d MB, phi %d MB)" % (8 * ng ** 3 >> 20, 8 * ng ** 3 >> 20),
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "gpu_launches": primary["launches"],

@@ -135,8 +135,10 @@ typedef struct {
     int status;              /* the call's return code                          */
     double eps_ref;          /* nDGP: rms(Omega_m a^-1 delta / beta);
                                 Kmouflage: rms(3 beta A Omega_m a^-1 delta/c~)  */
-    double eps[65];          /* eps[0] initial, then after each cycle (MIXED:
-                                after each defect correction)                   */
+    double eps[65];          /* eps[0] initial, then after each measured cycle
+                                (FP64: the norm pass is skipped on cycles
+                                predicted far from the tolerance; MIXED: after
+                                each defect correction)                         */
     int n_eps;               /* entries of eps[] written                        */
     double c_final;          /* <N(phi)>, the compatibility constant            */
     double mean_shift;       /* mean removed from phi (gauge <phi> = 0)          */

@@ -407,9 +407,38 @@ k_prolong(T *U0, T *U1, const T *__restrict__ UH0, const T *__restrict__ UH1, co
     prolong_cell<T>(U0, U1, UH0, UH1, RH0, RH1, n, iz & 1, iz >> 1, j, m);
 }
 
+// four fine cells per thread (FP32, fine rows a multiple of 4 long)
+__global__ void __launch_bounds__(256)
+k_prolong4(float *U0, float *U1, const float *__restrict__ UH0, const float *__restrict__ UH1,
+           const float *__restrict__ RH0, const float *__restrict__ RH1, int n)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int iz = blockIdx.z;
+    if (4 * q >= n / 2 || j >= n) return;
+    prolong_quad(U0, U1, UH0, UH1, RH0, RH1, n, iz & 1, iz >> 1, j, 4 * q);
+}
+
+template <typename T>
+bool launch_prolong4(const LevArrays<T> &, const LevArrays<T> &, cudaStream_t)
+{
+    return false;
+}
+
+template <>
+bool launch_prolong4<float>(const LevArrays<float> &Lf, const LevArrays<float> &Lc, cudaStream_t st)
+{
+    if (Lf.half % 4 != 0 || Lf.ncol >= (1LL << 31)) return false;
+    const dim3 b = block_mj(Lf.half / 4);
+    const dim3 g = grid_mj(Lf.half / 4, Lf.n, b, 2 * Lf.n);
+    k_prolong4<<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], Lf.n);
+    return true;
+}
+
 template <typename T>
 void launch_prolong(const LevArrays<T> &Lf, const LevArrays<T> &Lc, cudaStream_t st)
 {
+    if (launch_prolong4<T>(Lf, Lc, st)) return;
     const dim3 b = block_mj(Lf.half);
     const dim3 g = grid_mj(Lf.half, Lf.n, b, 2 * Lf.n);
     k_prolong<T><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], Lf.n);
