@@ -276,8 +276,15 @@ def main():
         return {"value": upd / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * ng ** 3,
                 "d2h_bytes_per_step": 8 * ng ** 3}
 
+    # DRAM bytes (read + write) per launch of the dominant kernels from ncu at
+    # 256^3 (profiles/k_smooth2_fp64_ndgp_256.md, k_smooth4_fp32corr_ndgp_256.md),
+    # scaled by the cell count to this mesh
+    TRAFFIC_256 = {"fp64": 202.4e6 + 50.3e6, "mixed": 202.4e6 + 24.8e6}
+
     def roofline(r, precision, fp64_tf):
         ms = r["avg_launch_ms"]
+        traffic = TRAFFIC_256[precision] * (ng / 256.0) ** 3
+        tsrc = "ncu dram__bytes_read.sum + dram__bytes_write.sum at 256^3, scaled by (ng/256)^3"
         if precision == "fp64":
             # finest FP64 half-sweep: read both colours + the colour's s,
             # write the colour = 2 s n^3 bytes (s = 8); FP64-pipe bound
@@ -285,7 +292,7 @@ def main():
             gbs = alg / (ms * 1e-3) / 1e9
             tf = FLOPS_PER_CELL_FP64 * (ng ** 3 / 2) / (ms * 1e-3) / 1e12
             return {"bound": "alu", "achieved": tf, "peak": fp64_tf, "unit": "TFLOP/s", "frac": tf / fp64_tf,
-                    "traffic": None, "kernel": "k_smooth2<double> finest half-sweep",
+                    "traffic": traffic, "traffic_source": tsrc, "kernel": "k_smooth2<double> finest half-sweep",
                     "peak_source": "FP64 FMA rate measured by mg_probe_alu_peaks on this GPU",
                     "alg_flops_per_cell": FLOPS_PER_CELL_FP64, "avg_launch_ms": ms, "launches": r["fine_launches"],
                     "hbm_view": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
@@ -296,7 +303,7 @@ def main():
         alg = 14 * ng ** 3
         gbs = alg / (ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                "traffic": None, "kernel": "k_smooth4<float, correction, nDGP> finest half-sweep",
+                "traffic": traffic, "traffic_source": tsrc, "kernel": "k_smooth4<float, correction, nDGP> finest half-sweep",
                 "peak_source": peak_src, "avg_launch_ms": ms, "launches": r["fine_launches"],
                 "alg_bytes_per_launch": alg}
 
