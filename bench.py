@@ -148,6 +148,19 @@ def cpu_baseline(delta_host, a, sample_cycles=1):
             "seconds": dt}
 
 
+def reduce_over_ranks(dist, ms, updates, device):
+    """Whole-job numbers of a replicas run: the slowest rank's time (max) and
+    the updates of all ranks (sum); the identity without a process group."""
+    import torch
+    if not dist:
+        return ms, float(updates)
+    mx = torch.tensor([ms], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[0])
+
+
 def workload_name(a):
     return ("nDGP FAS V(2,2) solve to eps/eps_ref<%g, %d^3 mesh, CIC of %d^3 Zel'dovich particles "
             "(P~k^0.96 e^-k/5, sigma8=0.8, z=0), L=%g Mpc/h, a=1, Omega_m=0.3, H0 rc=%g"
@@ -162,6 +175,8 @@ def run_reference(a, rank, world):
     pos = particles(a, 0)
     delta, _ = oracle.cic_deposit(pos, a.ng, a.np)
     vals = []
+    for _ in range(a.warmup):
+        cpu_baseline(delta, a)
     t0 = time.perf_counter()
     for _ in range(a.steps):
         cb = cpu_baseline(delta, a)
@@ -211,13 +226,7 @@ def main():
     hbm_peak, peak_src = peaks()
 
     def reduce_max_sum(x, y):
-        t = torch.tensor([x, float(y)], dtype=torch.float64, device=dev)
-        if not dist:
-            return x, float(y)
-        mx, sm_ = t.clone(), t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
-        return float(mx[0]), float(sm_[1])
+        return reduce_over_ranks(dist, x, y, dev)
 
     def timed(precision):
         """W untimed + K timed solves; CUDA events on the caller's stream
