@@ -18,3 +18,11 @@ def orc():
     import oracle
     oracle.lib()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def paper():
+    """Values the paper prints for its code tests (tests/golden, cited)."""
+    import json
+    with open(os.path.join(ROOT, "tests", "golden", "paper_code_tests.json")) as f:
+        return json.load(f)

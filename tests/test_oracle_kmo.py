@@ -135,42 +135,46 @@ def test_kmo_manufactured_3d(orc, n_kmo):
     assert 3.5 < errs[0] / errs[1] < 4.5 and 3.8 < errs[1] / errs[2] < 4.2, errs
 
 
-def _cardano(f, gamma):
+def _cardano(f, gamma, k):
     """Sec. 4.2.3 printed root of gamma y^3 + y = f:
-    y = g^(1/3)/(6 gamma) - 2/g^(1/3), g = gamma^2[108 f + 20.78460969
-    sqrt(27 f^2 + 4/gamma)] (20.78460969 = 12 sqrt(3))."""
-    g = gamma ** 2 * (108 * f + 20.78460969 * np.sqrt(27 * f ** 2 + 4 / gamma))
+    y = g^(1/3)/(6 gamma) - 2/g^(1/3), g = gamma^2[108 f + k
+    sqrt(27 f^2 + 4/gamma)] with the printed k = 20.78460969 (= 12 sqrt(3))."""
+    g = gamma ** 2 * (108 * f + k * np.sqrt(27 * f ** 2 + 4 / gamma))
     return np.cbrt(g) / (6 * gamma) - 2 / np.cbrt(g)
 
 
-def test_kmo_sphere_cubic_root(orc):
+def test_kmo_sphere_cubic_root(orc, paper):
     """The printed spherical solution (Sec. 4.2.3) is the real root of the
-    cubic gamma y^3 + y = f that Eq. Kmo_eom_spherical1 gives for n = 2."""
+    cubic gamma y^3 + y = f that Eq. Kmo_eom_spherical1 gives for n = 2;
+    its printed constant is 12 sqrt(3) to the printed digits."""
+    k = paper["kmouflage_sphere_test"]["cardano_constant"]
+    assert abs(k - 12 * np.sqrt(3)) < 1e-8
     for gamma in (1.0, 10.0, 100.0):
         for f in (1e-3, 0.1, 1.0, 30.0):
-            y = _cardano(f, gamma)
+            y = _cardano(f, gamma, k)
             assert gamma * y ** 3 + y == pytest.approx(f, rel=1e-7)
 
 
-def test_kmo_sphere_shape(orc):
+def test_kmo_sphere_shape(orc, paper):
     """Sec. 4.2.3: delta = 5000 in a sphere of R = 0.1 N, n = 2, beta = 0.2,
     K0 = 1, 10, 100 (gamma = K0 at a = lambda = 1).  The radial gradient of
     the solution near the centre agrees with the cubic root to a few per
     cent (periodic images and O(h^2) limit it)."""
-    n, a, om, beta, L = 64, 1.0, 0.3, 0.2, 64.0
-    R = 0.1 * n
-    delta = inputs.tophat_sphere(n, R, 5000.0)
+    t = paper["kmouflage_sphere_test"]
+    n, a, om, beta, L = 64, 1.0, 0.3, t["beta"], 64.0
+    R = t["R_over_Ng"] * n
+    delta = inputs.tophat_sphere(n, R, t["delta"])
     dbar = delta.mean()
     ct = orc.c_tilde(n, L)
     c = n // 2
-    for K0 in (1.0, 10.0, 100.0):
-        gamma = orc.gamma_kmo(2, K0, a, 1.0)
-        u, _ = orc.kmo_solve(delta, a, om, L, 2, K0, beta, 1.0, 0.0, 1.0, orc.Opts(rtol=1e-10))
+    for K0 in t["K0"]:
+        gamma = orc.gamma_kmo(t["n"], K0, a, 1.0)
+        u, _ = orc.kmo_solve(delta, a, om, L, t["n"], K0, beta, 1.0, 0.0, 1.0, orc.Opts(rtol=1e-10))
         for m in (1, 2, 3, 4):
             r = np.sqrt(m ** 2 + 0.5)
-            d_enc = (5000.0 * min(1.0, (R / r) ** 3)) - dbar    # mean delta - <delta> within r
+            d_enc = (t["delta"] * min(1.0, (R / r) ** 3)) - dbar    # mean delta - <delta> within r
             f = beta * om / ct * d_enc * r
-            expect = _cardano(f, gamma) * m / r
+            expect = _cardano(f, gamma, t["cardano_constant"]) * m / r
             got = u[c + m, c, c] - u[c + m - 1, c, c]
             assert got == pytest.approx(expect, rel=0.06), (K0, m, got, expect)
 
