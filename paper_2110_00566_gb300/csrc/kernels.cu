@@ -95,7 +95,7 @@ k_smooth2(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un
 // four cells of an FP32 colour row per thread (rows whose length is a
 // multiple of 4, colour arrays below 2^31 elements)
 template <bool CORR, int MODEL>
-__global__ void __launch_bounds__(256) k_smooth4(const float *__restrict__ Uc, const float *__restrict__ Uo, float *__restrict__ Un,
+__global__ void __launch_bounds__(256, MODEL == 0 ? 4 : 2) k_smooth4(const float *__restrict__ Uc, const float *__restrict__ Uo, float *__restrict__ Un,
           const float *__restrict__ Sc, const float *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<float> L,
           const OpK<float> *__restrict__ opp, int colour, const float *__restrict__ Bc, const float *__restrict__ Bo)
 {
@@ -112,12 +112,11 @@ bool launch_smooth4(const LevArrays<T> &, const LevK<T> &, const OpK<T> *, int, 
     return false;
 }
 
-template <>
-bool launch_smooth4<float>(const LevArrays<float> &L, const LevK<float> &K, const OpK<float> *op, int colour, int nb,
-                           cudaStream_t st)
+static bool launch_smooth4_bx(const LevArrays<float> &L, const LevK<float> &K, const OpK<float> *op, int colour,
+                              int nb, int bx, cudaStream_t st)
 {
     if (L.half % 4 != 0 || L.ncol >= (1LL << 31)) return false;
-    const dim3 b = block_mj(L.half / 4);
+    const dim3 b = bx > 0 ? dim3(bx, 256 / bx, 1) : block_mj(L.half / 4);
     const dim3 g = grid_mj(L.half / 4, L.n, b, L.n);
     const float *U0 = L.U(colour), *U1 = L.U(1 - colour);
     float *Un = L.u[nb][colour];
@@ -135,6 +134,18 @@ bool launch_smooth4<float>(const LevArrays<float> &L, const LevK<float> &K, cons
     }
 #undef MG_SMOOTH4
     return true;
+}
+
+template <>
+bool launch_smooth4<float>(const LevArrays<float> &L, const LevK<float> &K, const OpK<float> *op, int colour, int nb,
+                           cudaStream_t st)
+{
+    return launch_smooth4_bx(L, K, op, colour, nb, L.qbx, st);
+}
+
+bool launch_smooth4_shape(const LevArrays<float> &L, const OpK<float> *op, int colour, int bx, cudaStream_t st)
+{
+    return launch_smooth4_bx(L, make_levk<float>(L.n, L.h), op, colour, 1 - L.cur[colour], bx, st);
 }
 
 template <typename T>

@@ -23,6 +23,7 @@ struct LevArrays {
     T *base[2];          // correction form: base field (nullptr: plain form)
     LevScal *sc;         // this level's device scalars
     int model = -1;      // operator of the uploaded OpK (0 nDGP, 1 Kmouflage), -1 unknown
+    int qbx = 0;         // FP32 four-cell smoother: threads along a row (autotuned; 0 = default)
     T *U(int colour) const { return u[cur[colour]][colour]; }
 };
 
@@ -33,6 +34,10 @@ template <typename T>
 void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, int colour, cudaStream_t st);
 template <typename T>
 void launch_smooth_shape(const LevArrays<T> &L, const OpK<T> *op, int colour, int bx, cudaStream_t st);
+// FP32 four-cell half-sweep with bx threads along a row (256 / bx rows) into
+// the alternate buffer, leaving the buffer state untouched (autotuner);
+// false when the level does not use the four-cell kernel
+bool launch_smooth4_shape(const LevArrays<float> &L, const OpK<float> *op, int colour, int bx, cudaStream_t st);
 // residual norm; with D set also writes -d (with the old c) as FP32,
 // colour-split
 template <typename T>

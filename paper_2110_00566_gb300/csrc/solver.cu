@@ -468,6 +468,40 @@ static int solve_plain(mg_ctx *ctx, int n, const ModelDesc &md, const double *de
     return rc;
 }
 
+// Block shape of the FP32 four-cell smoother per level (threads along a row:
+// 8, 16, 32 or 64; 256 per block), picked once per pyramid by timing
+// half-sweeps on the level's own arrays (into the alternate buffer) before
+// any cycle is captured.  Levels below 64^3 keep the default.
+static void tune_smooth4(mg_ctx *ctx, Pyramid<float> &P)
+{
+    cudaStream_t s = ctx->stream;
+    for (auto &L : P.L) {
+        if (L.qbx != 0 || L.n < 64) continue;
+        int best = 0;
+        float best_ms = 1e30f;
+        for (int bx : {8, 16, 32, 64}) {
+            if (bx > L.half / 4) continue;
+            if (!launch_smooth4_shape(L, P.opT, 0, bx, s)) break;
+            float t = 1e30f;
+            for (int r = 0; r < 3; ++r) {
+                MG_CK(cudaEventRecord(ctx->t0, s));
+                launch_smooth4_shape(L, P.opT, r & 1, bx, s);
+                MG_CK(cudaEventRecord(ctx->t1, s));
+                MG_CK(cudaEventSynchronize(ctx->t1));
+                float ms = 0.f;
+                MG_CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
+                t = std::min(t, ms);
+            }
+            MG_CK(cudaGetLastError());
+            if (t < best_ms) {
+                best_ms = t;
+                best = bx;
+            }
+        }
+        L.qbx = best > 0 ? best : -1;
+    }
+}
+
 // Mixed precision (defect correction / iterative refinement): the FP64
 // master field u and the FP64 finest-level defect d = L(u) drive FP32 FAS
 // cycles on the correction e, which solve L(u + e) - L(u) = -d with the base
@@ -484,6 +518,7 @@ int solve_mixed(mg_ctx *ctx, int n, const ModelDesc &md, const double *delta, do
     const long long cnt = (long long)n * n * n;
     upload_op(ctx, P64, md);
     upload_op(ctx, P32, md);
+    tune_smooth4(ctx, P32);
     MG_CK(cudaMemsetAsync(P64.scal, 0, sizeof(LevScal) * P64.nlev, s));
     MG_CK(cudaMemsetAsync(P32.scal, 0, sizeof(LevScal) * P32.nlev, s));
     MG_CK(cudaEventRecord(ctx->t0, s));
