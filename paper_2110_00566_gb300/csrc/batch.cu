@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(BTHREADS, 2) k_batch(BatchArgs A)
             const double c_old = I.sc64->c;
             double acc[4] = {0.0, 0.0, 0.0, 0.0};
             if (m < L0.half && j < L0.n)
-                resid_cell<double, false>(I.opd, K, I.u64[0], I.u64[1], I.s64[0], I.s64[1], nullptr, nullptr, nullptr,
+                resid_cell<double, false, 0>(I.opd, K, I.u64[0], I.u64[1], I.s64[0], I.s64[1], nullptr, nullptr, nullptr,
                                           nullptr, L0.f[0], L0.f[1], c_old, z & 1, z >> 1, j, m, acc);
             double tot[4];
             const int nt = mj_tiles(L0, 2 * L0.n);
@@ -352,12 +352,27 @@ __global__ void __launch_bounds__(BTHREADS, 2) k_batch(BatchArgs A)
             return;
         }
         // PH_PROLONG: level d += P(level d+1)
-        const int total = prefix([&](int q) { return d < A.inst[q].nlev - 1 ? mj_tiles(A.inst[q].lev[d], 2 * A.inst[q].lev[d].n) : 0; });
+        const int total = prefix([&](int q) {
+            const BLev &L = A.inst[q].lev[d];
+            return d < A.inst[q].nlev - 1 ? (quad_level(L) ? 2 * quad_tiles(L) : mj_tiles(L, 2 * L.n)) : 0;
+        });
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
             const int q = find_inst(pref, count, t);
             const BInst &I = A.inst[q];
             const BLev &L = I.lev[d];
             const BLev &C = I.lev[d + 1];
+            if (quad_level(L)) {
+                // flat quad index over (colour, i, j, m0 / 4)
+                const int qr = L.half / 4;
+                const int Q = (t - pref[q]) * BTHREADS + (int)threadIdx.x;
+                const int per = L.n * L.n * qr;
+                if (Q < 2 * per) {
+                    const int col = Q / per, rem = Q % per, r = rem / qr;
+                    prolong_quad(L.u[P.cur[0]][0], L.u[P.cur[1]][1], C.u[P.curc[0]][0], C.u[P.curc[1]][1], C.ur[0],
+                                 C.ur[1], L.n, col, r / L.n, r % L.n, 4 * (rem % qr));
+                }
+                continue;
+            }
             const int gx = cdiv(L.half, L.tx), gy = cdiv(L.n, BTHREADS / L.tx);
             int m, j, z;
             tile_xyz(t - pref[q], gx, gy, L.tx, m, j, z);
