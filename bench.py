@@ -140,7 +140,7 @@ def cpu_baseline(delta_host, a, sample_cycles=1):
     levels = oracle.num_levels(ng)
     for l in range(levels):
         cells = (ng >> l) ** 3
-        per_cycle += (64 if l == levels - 1 else 4) * cells
+        per_cycle += (oracle.Opts().coarse_sweeps if l == levels - 1 else 4) * cells
     updates = per_cycle * st.cycles
     return {"value": updates / dt / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": "%d V(2,2) cycle(s) of the %d^3 solve (with its initial and final residual passes), "

@@ -126,7 +126,7 @@ typedef struct {
 } mg_opts;
 
 /* pre = post = 2, max_cycles = 30, V, FP64, rtol = 1e-8, atol = 0,
- * warm_start = 0, coarse_sweeps = 64, use_graph = 1, inner_cycles = 0. */
+ * warm_start = 0, coarse_sweeps = 16, use_graph = 1, inner_cycles = 0. */
 void mg_opts_default(mg_opts *o);
 
 typedef struct {

@@ -203,7 +203,7 @@ class Opts:
     post: int = 2
     max_cycles: int = 30
     cycle: int = 0            # 0 = V, 1 = F, 2 = W
-    coarse_sweeps: int = 64
+    coarse_sweeps: int = 16
     rtol: float = 1e-8
     atol: float = 0.0
 

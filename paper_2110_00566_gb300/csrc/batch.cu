@@ -36,6 +36,9 @@ struct BLev {
     int n, half;
     double h;
     int tx;          // tile width along m (threads); 256 / tx along j
+    LevK<float> K;   // the level's stencil constants (computed on the host:
+                     // their FP64 divisions would cost more per tile than
+                     // the FP32 stencil work at the FP64 rate of this GPU)
 };
 
 struct BInst {
@@ -44,6 +47,7 @@ struct BInst {
     double *u64[2];
     double *s64[2];
     LevScal *sc64;
+    LevK<double> K64;    // finest-level constants (h = 1)
     OpK<float> opf;
     OpK<double> opd;
     double tol;
@@ -154,24 +158,33 @@ __global__ void __launch_bounds__(BTHREADS, 2) k_batch(BatchArgs A)
 
     // FP64 defect on level 0 of every active instance, -d into the FP32
     // source; the finaliser checks convergence
+    // a defect tile covers DEF_Z consecutive (colour, plane) values of one
+    // (m, j) tile: each thread sums its cells before the tile's block
+    // reduction, whose FP64 shuffles would otherwise cost about half as
+    // much as the defect itself
+    constexpr int DEF_Z = 32;
+    auto defect_tiles = [&](const BLev &L0) { return mj_tiles(L0, 1) * cdiv(2 * L0.n, DEF_Z); };
     auto defect = [&]() {
-        const int total = prefix([&](int q) { return mj_tiles(A.inst[q].lev[0], 2 * A.inst[q].lev[0].n); });
+        const int total = prefix([&](int q) { return defect_tiles(A.inst[q].lev[0]); });
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
             const int q = find_inst(pref, count, t);
             BInst &I = A.inst[q];
             const BLev &L0 = I.lev[0];
             const int lt = t - pref[q];
             const int gx = cdiv(L0.half, L0.tx), gy = cdiv(L0.n, BTHREADS / L0.tx);
-            int m, j, z;
-            tile_xyz(lt, gx, gy, L0.tx, m, j, z);
-            const LevK<double> K = make_levk<double>(L0.n, 1.0);
+            const int plane = gx * gy;
+            int m, j, z0;
+            tile_xyz(lt % plane, gx, gy, L0.tx, m, j, z0);
+            const int zb = (lt / plane) * DEF_Z, ze = min(2 * L0.n, zb + DEF_Z);
+            const LevK<double> &K = I.K64;
             const double c_old = I.sc64->c;
             double acc[4] = {0.0, 0.0, 0.0, 0.0};
             if (m < L0.half && j < L0.n)
-                resid_cell<double, false, 0>(I.opd, K, I.u64[0], I.u64[1], I.s64[0], I.s64[1], nullptr, nullptr, nullptr,
-                                          nullptr, L0.f[0], L0.f[1], c_old, z & 1, z >> 1, j, m, acc);
+                for (int z = zb; z < ze; ++z)
+                    resid_cell<double, false, 0>(I.opd, K, I.u64[0], I.u64[1], I.s64[0], I.s64[1], nullptr, nullptr,
+                                                 nullptr, nullptr, L0.f[0], L0.f[1], c_old, z & 1, z >> 1, j, m, acc);
             double tot[4];
-            const int nt = mj_tiles(L0, 2 * L0.n);
+            const int nt = defect_tiles(L0);
             if (tile_sum<4>(acc, I.partials, I.counter, lt, nt, tot) && threadIdx.x == 0) {
                 const double cnt = (double)L0.n * L0.n * L0.n;
                 const double c_new = tot[0] / cnt, dc = c_new - c_old;
@@ -256,7 +269,7 @@ __global__ void __launch_bounds__(BTHREADS, 2) k_batch(BatchArgs A)
                 const int q = find_inst(pref, count, t);
                 const BInst &I = A.inst[q];
                 const BLev &L = I.lev[d];
-                const LevK<float> K = make_levk<float>(L.n, L.h);
+                const LevK<float> &K = L.K;
                 if (quad_level(L)) {
                     // flat quad index: row (i, j), quad m0 / 4 fastest
                     const int qr = L.half / 4;
@@ -294,7 +307,7 @@ __global__ void __launch_bounds__(BTHREADS, 2) k_batch(BatchArgs A)
                 const double c_old = L.sc->c;
                 const double cshift = c_old - L.sc->fshift;
                 double acc[4] = {0.0, 0.0, 0.0, 0.0};
-                const LevK<float> Kf = make_levk<float>(L.n, L.h);
+                const LevK<float> &Kf = L.K;
                 if ((nc & 3) == 0) {
                     // flat index over (I, J, K0 / 4), four coarse cells per thread
                     const int qr = nc / 4;
@@ -336,12 +349,13 @@ __global__ void __launch_bounds__(BTHREADS, 2) k_batch(BatchArgs A)
                 int m, j, z;
                 tile_xyz(lt, gx, gy, C.tx, m, j, z);
                 const float dcf = (float)I.lev[d].sc->dc;
-                double acc[2] = {0.0, 0.0};
+                CsAcc<float> ca;
                 if (m < C.half && j < C.n) {
-                    const LevK<float> Kf = make_levk<float>(C.n, C.h);
+                    const LevK<float> &Kf = C.K;
                     cs_cell<float, true>(I.opf, Kf, C.ur[0], C.ur[1], C.s[0], C.s[1], C.f[0], C.f[1], C.base[0],
-                                         C.base[1], dcf, z & 1, z >> 1, j, m, acc);
+                                         C.base[1], dcf, z & 1, z >> 1, j, m, ca);
                 }
+                double acc[2] = {ca.sum(), (double)ca.cl};
                 double tot[2];
                 if (tile_sum<2>(acc, I.partials, I.counter, lt, mj_tiles(C, 2 * C.n), tot) && threadIdx.x == 0) {
                     const double c = tot[0] / ((double)C.n * C.n * C.n);
@@ -623,7 +637,9 @@ int solve_batch(mg_ctx *ctx, int count, const mg_instance *inst, const mg_opts &
             bl.half = L.half;
             bl.h = L.h;
             bl.tx = w->tx[q][l];
+            bl.K = make_levk<float>(L.n, L.h);
         }
+        B.K64 = make_levk<double>(n, 1.0);
         B.u64[0] = Uu[0];
         B.u64[1] = Uu[1];
         B.s64[0] = U64.s[0];

@@ -373,10 +373,11 @@ k_coarse_source(const T *__restrict__ UR0, const T *__restrict__ UR1, const T *_
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const T dcf = (T)scf->dc;
-    double acc[2] = {0.0, 0.0};
+    CsAcc<T> ca;
     if (m < L.half && j < L.n)
         for (int iz = blockIdx.z; iz < 2 * L.n; iz += gridDim.z)
-            cs_cell<T, CORR>(op, L, UR0, UR1, S0, S1, F0, F1, B0, B1, dcf, iz & 1, iz >> 1, j, m, acc);
+            cs_cell<T, CORR>(op, L, UR0, UR1, S0, S1, F0, F1, B0, B1, dcf, iz & 1, iz >> 1, j, m, ca);
+    double acc[2] = {ca.sum(), (double)ca.cl};
     double tot[2];
     if (grid_sum<2>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
         const double c = tot[0] / ((double)L.n * L.n * L.n);

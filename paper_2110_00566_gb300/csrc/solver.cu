@@ -695,7 +695,7 @@ void mg_opts_default(mg_opts *o)
     o->rtol = 1e-8;
     o->atol = 0.0;
     o->warm_start = 0;
-    o->coarse_sweeps = 64;
+    o->coarse_sweeps = 16;
     o->use_graph = 1;
     o->inner_cycles = 0;
 }
