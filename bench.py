@@ -288,7 +288,7 @@ def main():
     # DRAM bytes (read + write) per launch of the dominant kernels from ncu at
     # 256^3 (profiles/k_smooth2_fp64_ndgp_256.md, k_smooth4_fp32corr_ndgp_256.md),
     # scaled by the cell count to this mesh
-    TRAFFIC_256 = {"fp64": 202.4e6 + 50.3e6, "mixed": 202.4e6 + 24.8e6}
+    TRAFFIC_256 = {"fp64": 202.4e6 + 50.3e6, "mixed": 202.4e6 + 24.1e6}
 
     def roofline(r, precision, fp64_tf):
         ms = r["avg_launch_ms"]
