@@ -275,6 +275,17 @@ def kmo_solve(delta, a, omega_m, box_mpch, n, k0, beta_kmo, lam, phibar_prime_ov
     return mg_solve(op, s0, eps_ref, opts, u0)
 
 
+def kmo_linear_solve(delta, a, omega_m, box_mpch, n, k0, beta_kmo, lam, phibar_prime_over_h0, A_bar):
+    """Linear-theory Kmouflage field (Eq. kmf_eqn_codeunit_lin): the gradient
+    term of Sigma_1 and Sigma_2 dropped,
+        Lap phi~ = 3 beta A Omega_m a^-1 delta / [c~ (1 + gamma (phibar'^2/H0^2)^(n-1))],
+    solved with the 7-point Green's function (the multigrid Laplacian)."""
+    ng = delta.shape[0]
+    s0, _ = kmo_source(delta, a, omega_m, ng, box_mpch, beta_kmo, A_bar)
+    k1 = 1.0 + gamma_kmo(n, k0, a, lam) * (phibar_prime_over_h0 ** 2) ** (n - 1)
+    return fft_poisson(s0 / k1)
+
+
 # ---------------------------------------------------------------------------
 # particle-mesh pieces (Sec. 3.1, 3.1.1)
 # ---------------------------------------------------------------------------

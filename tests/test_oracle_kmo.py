@@ -202,3 +202,25 @@ def test_kmo_mg_matches_newton(orc, n_kmo, amp, gamma):
     assert np.linalg.norm(u - un) < 1e-10 * np.linalg.norm(un)
     lin = orc.fft_poisson(s0 / (1 + gamma * 0.01 ** (n_kmo - 1)))
     assert np.linalg.norm(u - lin) > 1e-3 * np.linalg.norm(lin)
+
+
+def test_kmo_linear_is_the_small_amplitude_limit(orc):
+    """Eq. kmf_eqn_codeunit_lin: for a small density field the full
+    multigrid solve approaches the linear FFT solution, with a relative
+    difference that falls as the square of the amplitude (the leading
+    nonlinear terms are quadratic in the field), and the linear solution is
+    exactly linear in delta."""
+    n, a, om, L = 16, 1.0, 0.3, 16.0
+    nk, k0, beta, lam, bp, A = 2, 10.0, 0.2, 1.0, 0.3, 1.0
+    base = inputs.white_noise(n, 91)
+    diffs = []
+    for amp in (1e3, 1e2, 1e1):
+        d = amp * base
+        lin = orc.kmo_linear_solve(d, a, om, L, nk, k0, beta, lam, bp, A)
+        u, _ = orc.kmo_solve(d, a, om, L, nk, k0, beta, lam, bp, A, orc.Opts(rtol=1e-12, max_cycles=60))
+        diffs.append(np.linalg.norm(u - lin) / np.linalg.norm(lin))
+    assert diffs[1] == pytest.approx(diffs[0] / 100, rel=0.2)
+    assert diffs[2] == pytest.approx(diffs[1] / 100, rel=0.2)
+    l1 = orc.kmo_linear_solve(base, a, om, L, nk, k0, beta, lam, bp, A)
+    l3 = orc.kmo_linear_solve(3 * base, a, om, L, nk, k0, beta, lam, bp, A)
+    assert np.abs(l3 - 3 * l1).max() < 1e-12 * np.abs(l3).max()
