@@ -437,9 +437,26 @@ def main():
                              "final_eps_over_eps_ref": st.eps[st.n_eps - 1] / st.eps_ref}
                 phis[prec] = phi
             l2 = float(torch.linalg.vector_norm(phis["mixed"] - phis["fp64"]) / torch.linalg.vector_norm(phis["fp64"]))
+            # screening off: the linear-theory field (FFT), and the rms
+            # gradient (fifth force) of the full field relative to it
+            lin = torch.empty_like(dk)
+            args = (ng, box, 1.0, 0.3, nk, k0, 0.2, lam, -1e-3, float(np.exp(-0.02)))
+            B.mg_solve_kmouflage_linear(ctx, *args, dk, lin)
+            torch.cuda.synchronize(dev)
+            e0.record()
+            B.mg_solve_kmouflage_linear(ctx, *args, dk, lin)
+            e1.record()
+            torch.cuda.synchronize(dev)
+
+            def grad_rms(f):
+                g = [torch.roll(f, -1, d) - torch.roll(f, 1, d) for d in range(3)]
+                return float(torch.sqrt(sum((x * x).mean() for x in g)))
+
             out["n%d_K0_%g" % (nk, k0)] = {"fp64": res["fp64"], "mixed": res["mixed"],
                                           "mixed_speedup": res["fp64"]["ms"] / res["mixed"]["ms"],
-                                          "phi_rel_l2_mixed_vs_fp64": l2, "unit": UNIT}
+                                          "phi_rel_l2_mixed_vs_fp64": l2, "unit": UNIT,
+                                          "linear_ms": e0.elapsed_time(e1),
+                                          "fifth_force_rms_full_over_linear": grad_rms(phis["fp64"]) / grad_rms(lin)}
         out["config"] = "512^3 mesh, L = %g Mpc/h, beta = 0.2, a = 1" % box
         return out
 

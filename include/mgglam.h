@@ -196,6 +196,17 @@ int mg_solve_kmouflage(mg_ctx *ctx, const mg_grid *g, const mg_kmo_params *p,
                        mg_stats *stats);
 
 /*
+ * Linear-theory Kmouflage field (Eq. kmf_eqn_codeunit_lin): the gradient
+ * term of the denominator and the T term dropped,
+ *   Lap phi = 3 beta A Omega_m a^-1 (delta - <delta>) / [c~ (1 + gamma (phibar'/H0)^(2(n-1)))],
+ * solved by FFT with the 7-point Green's function (the multigrid Laplacian);
+ * the screening-off reference for mg_solve_kmouflage.  ng even >= 2.
+ * Errors: MG_ERR_ARG, MG_ERR_CUDA, MG_ERR_OOM.
+ */
+int mg_solve_kmouflage_linear(mg_ctx *ctx, const mg_grid *g, const mg_kmo_params *p,
+                              const double *delta, double *phi);
+
+/*
  * Cloud-in-cell density contrast (Sec. 3.1): each of the np particles
  * (FP32 positions in [0, ng), np x 3) carries (ng^3/np) mean cell masses
  * spread over the 8 cells around it; delta_out = rho/rho_bar - 1 (ng^3,

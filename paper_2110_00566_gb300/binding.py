@@ -96,6 +96,7 @@ def _declare(L):
         "mg_solve_dgp": (C.c_int, [_VP, C.c_int, _P(mg_instance), _P(mg_opts), _P(mg_stats)]),
         "mg_solve_kmouflage": (C.c_int, [_VP, _P(mg_grid), _P(mg_kmo_params), _P(mg_opts), _VP, _VP,
                                          _P(mg_stats)]),
+        "mg_solve_kmouflage_linear": (C.c_int, [_VP, _P(mg_grid), _P(mg_kmo_params), _VP, _VP]),
         "pm_cic_deposit": (C.c_int, [_VP, C.c_int, _VP, C.c_longlong, _VP]),
         "pm_cic_index": (C.c_int, [_VP, C.c_int, _VP, C.c_longlong, _VP]),
         "pm_cic_deposit_noalloc": (C.c_int, [C.c_int, _VP, C.c_longlong, _VP, _VP]),
@@ -267,6 +268,15 @@ def mg_solve_kmouflage(ctx: Context, ng, box_mpch, a, omega_m, n, k0, beta_kmo, 
                                   C.byref(st))
     ctx._rc(rc)
     return rc, st
+
+
+def mg_solve_kmouflage_linear(ctx: Context, ng, box_mpch, a, omega_m, n, k0, beta_kmo, lam, phibar_prime_over_h0,
+                              A_bar, delta, phi):
+    _check_dtype(delta, "f64")
+    _check_dtype(phi, "f64")
+    g = mg_grid(int(ng), float(box_mpch), float(a), float(omega_m))
+    p = mg_kmo_params(int(n), float(k0), float(beta_kmo), float(lam), float(phibar_prime_over_h0), float(A_bar))
+    ctx._rc(lib().mg_solve_kmouflage_linear(ctx.h, C.byref(g), C.byref(p), _ptr(delta), _ptr(phi)))
 
 
 def pm_cic_deposit(ctx: Context, ng, pos, delta_out):

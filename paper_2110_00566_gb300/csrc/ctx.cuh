@@ -160,6 +160,7 @@ int check_opts(mg_ctx *ctx, const mg_opts &o);
 // Newtonian potential Lap Phi = (3/2) Omega_m a^-1 delta on device arrays
 void pm_fft_setup(mg_ctx *ctx, int n);
 void newton_potential_dev(mg_ctx *ctx, int n, double a, double om, const double *delta, double *out);
+void poisson_dev(mg_ctx *ctx, int n, double coef, const double *rhs, double *out);
 // the nDGP adjoint solve on device arrays (validated arguments)
 int adjoint_dev(mg_ctx *ctx, int n, double a, double om, double Rc, const mg_opts &o, const double *dphi,
                 const double *ddel, const double *dg, double *dout, double *drc, mg_stats *st);

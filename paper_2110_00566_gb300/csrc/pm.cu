@@ -226,17 +226,23 @@ void pm_fft_setup(mg_ctx *ctx, int n)
     w.fft_n = n;
 }
 
-// Lap Phi = (3/2) Omega_m a^-1 delta (Eq. GR_poisson_codeunit), solved with
-// the 7-point Green's function by FFT (Sec. 3.1); the zero mode is dropped.
-void newton_potential_dev(mg_ctx *ctx, int n, double a, double om, const double *delta, double *out)
+// Lap out = coef rhs with the 7-point Green's function by FFT (Sec. 3.1);
+// the zero mode is dropped (so the mean of rhs is ignored)
+void poisson_dev(mg_ctx *ctx, int n, double coef, const double *rhs, double *out)
 {
     PmWork &w = pmw(ctx);
-    const double scale = 1.5 * om / a / ((double)n * n * n);
-    MG_CUFFT(cufftExecD2Z(w.fwd, const_cast<double *>(delta), w.spec));
+    const double scale = coef / ((double)n * n * n);
+    MG_CUFFT(cufftExecD2Z(w.fwd, const_cast<double *>(rhs), w.spec));
     const long long modes = (long long)n * n * (n / 2 + 1);
     k_green<<<grid1(modes), 256, 0, ctx->stream>>>(w.spec, n, w.table, scale);
     MG_CK(cudaGetLastError());
     MG_CUFFT(cufftExecZ2D(w.inv, w.spec, out));
+}
+
+// Lap Phi = (3/2) Omega_m a^-1 delta (Eq. GR_poisson_codeunit)
+void newton_potential_dev(mg_ctx *ctx, int n, double a, double om, const double *delta, double *out)
+{
+    poisson_dev(ctx, n, 1.5 * om / a, delta, out);
 }
 
 static double E_lcdm(double a, double om) { return std::sqrt(om * std::pow(a, -3.0) + (1.0 - om)); }
@@ -309,6 +315,38 @@ int pm_cic_index(mg_ctx *ctx, int ng, const float *pos, long long np, int *idx_o
         k_cic_index<<<grid1(3 * np), 256, 0, ctx->stream>>>(dp, np, ng, di);
         MG_CK(cudaGetLastError());
         stage_out(ctx, idx_out, di, ib);
+        MG_CK(cudaStreamSynchronize(ctx->stream));
+        leave(ctx);
+    } catch (CudaFail &f) {
+        return f.code;
+    }
+    return MG_OK;
+}
+
+int mg_solve_kmouflage_linear(mg_ctx *ctx, const mg_grid *g, const mg_kmo_params *p, const double *delta,
+                              double *phi)
+{
+    if (!ctx) return MG_ERR_ARG;
+    if (!g || !p || !delta || !phi) return set_err(ctx, MG_ERR_ARG, "null argument");
+    if (g->ng < 2 || g->ng % 2 || p->n < 2 || p->k0 < 0 || !(g->a > 0) || !(g->box_mpch > 0) || !(p->lambda > 0))
+        return set_err(ctx, MG_ERR_ARG, "bad Kmouflage parameters");
+    try {
+        enter(ctx);
+        const int n = g->ng;
+        const double a = g->a;
+        double gam = p->n * p->k0, bp = 1.0;
+        for (int q = 0; q < p->n - 1; ++q) {
+            gam *= 1.0 / (2.0 * a * a * p->lambda * p->lambda);
+            bp *= p->phibar_prime_over_h0 * p->phibar_prime_over_h0;
+        }
+        const double ct = 2997.92458 * n / g->box_mpch;   // c~ = (c/H0) N / L
+        const double coef = 3.0 * p->beta_kmo * p->A_bar * g->omega_m / a / ct / (1.0 + gam * bp);
+        const size_t b = sizeof(double) * (size_t)n * n * n;
+        const double *dd = (const double *)stage_in(ctx, 0, delta, b, true);
+        double *dp = (double *)stage_in(ctx, 1, phi, b, false);
+        pm_fft_setup(ctx, n);
+        poisson_dev(ctx, n, coef, dd, dp);
+        stage_out(ctx, phi, dp, b);
         MG_CK(cudaStreamSynchronize(ctx->stream));
         leave(ctx);
     } catch (CudaFail &f) {

@@ -279,3 +279,20 @@ def test_cic_parity(B, ctx):
     out2 = np.empty_like(out)
     B.pm_cic_deposit(ctx, ng, pos, out2)
     assert np.array_equal(out, out2)
+
+
+@pytest.mark.parametrize("n,nk", [(16, 2), (32, 3)])
+def test_kmouflage_linear_solve(B, ctx, n, nk):
+    """The linear-theory Kmouflage field (Eq. kmf_eqn_codeunit_lin) against
+    the oracle's FFT solution, and the full solve approaching it for a small
+    density field."""
+    a, om, L = 1.0, 0.3, float(n)
+    pars = (nk, 10.0, 0.2, 1.0, 0.3, 1.0)
+    delta = 50.0 * inputs.white_noise(n, 95)
+    ref = oracle.kmo_linear_solve(delta, a, om, L, *pars)
+    out = np.empty_like(delta)
+    B.mg_solve_kmouflage_linear(ctx, n, L, a, om, *pars, delta, out)
+    assert l2(out, ref) < 1e-12
+    full = np.zeros_like(delta)
+    B.mg_solve_kmouflage(ctx, n, L, a, om, *pars, 0.01 * delta, full, B.opts(rtol=1e-12, max_cycles=60))
+    assert l2(full, 0.01 * ref) < 1e-4
