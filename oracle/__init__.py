@@ -348,23 +348,38 @@ def _wrap32(x, ng):
 
 
 def pm_step(pos, mom, ng, np_side, omega_m, a, da, model=1, rc_h0=1.0, first=False,
-            phi_guess=None, opts: Opts = None):
+            phi_guess=None, opts: Opts = None, kmo=None, box_mpch=None):
     """One leapfrog step in the scale factor (Sec. 3.1.1 code-unit equations
     of motion, with the drift sign of Eq. force_Kmo1):
         dp~/da = -(H0/adot) grad~ Phi~,   dx~/da = H0/(a^2 adot) p~,
     H0/adot = 1/(a E(a)).  Positions at a, momenta at a - da/2 (a - 0 when
     first=True) are advanced to a + da and a + da/2.  Phi = Phi_N + phi/2 for
-    nDGP (Eq. poisson_nDGP), Phi_N for GR (model 0).  FP32 state, FP64 force.
+    nDGP (Eq. poisson_nDGP), Phi_N for GR (model 0).  Kmouflage (model 2,
+    Eqs. force_Kmo2 and kmf_Poission_eqn_codeunit): Lap Phi_N = (3/2) A
+    Omega_m a^-1 delta, Phi = Phi_N + beta c~ phi~ with phi~ the Kmouflage
+    field, and the friction term dp~/da = -beta (dphibar/da) p~ taken in the
+    kick as the factor 1 - beta (dphibar/da) da_kick; kmo = dict(n, k0, beta,
+    lam, phibar_prime_over_h0, A_bar, dphibar_da), the background inputs at
+    a, and box_mpch the box (for c~).  FP32 state, FP64 force.
     Returns (pos, mom, phi)."""
     delta, _ = cic_deposit(pos, ng, np_side)
-    phin = newton_potential(delta, a, omega_m)
     phi = None
+    fr = 1.0
+    dak = 0.5 * da if first else da
+    if model == 2:
+        k = kmo
+        phin = newton_potential(delta, a, omega_m * k["A_bar"])
+        phi, _ = kmo_solve(delta, a, omega_m, box_mpch, k["n"], k["k0"], k["beta"], k["lam"],
+                           k["phibar_prime_over_h0"], k["A_bar"], opts, phi_guess)
+        phin = phin + (k["beta"] * c_tilde(ng, box_mpch)) * phi
+        fr = 1.0 - k["beta"] * k["dphibar_da"] * dak
+    else:
+        phin = newton_potential(delta, a, omega_m)
     if model == 1:
         phi, _ = dgp_solve(delta, a, omega_m, rc_h0, opts, phi_guess)
         phin = phin + 0.5 * phi
     acc = cic_force(phin, pos)
-    dak = 0.5 * da if first else da
-    mom = (mom.astype(np.float64) + acc * (dak / (a * E_lcdm(a, omega_m)))).astype(np.float32)
+    mom = (mom.astype(np.float64) * fr + acc * (dak / (a * E_lcdm(a, omega_m)))).astype(np.float32)
     am = a + 0.5 * da
     pos = (pos.astype(np.float64) + mom.astype(np.float64) * (da / (am ** 3 * E_lcdm(am, omega_m))))
     return _wrap32(pos, ng), mom, phi

@@ -133,3 +133,56 @@ def test_linear_growth_ndgp(orc):
     got = _plane_wave_growth(orc, model=1, rc=rc) / _plane_wave_growth(orc, model=0)
     assert got == pytest.approx(expect, rel=0.005)
     assert got > 1.05                      # enhanced growth, beta > 0
+
+
+def _kmo_pars(beta=0.2, dphibar_da=0.0, A_bar=1.02, bp=0.3):
+    return dict(n=2, k0=1.0, beta=beta, lam=1.0, phibar_prime_over_h0=bp, A_bar=A_bar, dphibar_da=dphibar_da)
+
+
+def _wave_load(ng, amp):
+    """One particle per cell, displaced by a small x plane wave."""
+    q = np.arange(ng) + 0.5
+    X, Y, Z = np.meshgrid(q, q, q, indexing="ij")
+    x = X + amp * np.sin(2 * np.pi * X / ng)
+    pos = np.stack([x % ng, Y, Z], -1).reshape(-1, 3).astype(np.float32)
+    return pos, np.zeros_like(pos)
+
+
+def test_kmo_step_reduces_to_gr_without_coupling(orc):
+    """beta = 0 and A = 1: the Kmouflage step is the GR step, bit for bit."""
+    ng = 16
+    pos, mom = _wave_load(ng, 0.2)
+    k = _kmo_pars(beta=0.0, dphibar_da=0.7, A_bar=1.0)
+    p0, m0, _ = orc.pm_step(pos, mom, ng, ng, 0.3, 0.5, 0.01, model=0, first=True)
+    p2, m2, _ = orc.pm_step(pos, mom, ng, ng, 0.3, 0.5, 0.01, model=2, first=True, kmo=k, box_mpch=64.0)
+    assert np.array_equal(p0, p2) and np.array_equal(m0, m2)
+
+
+def test_kmo_linear_force_ratio(orc):
+    """In the linear regime the Kmouflage kick is A (1 + 2 beta^2 / K1) times
+    the GR kick, K1 = 1 + gamma (phibar'/H0)^(2(n-1)): the fifth-force to
+    Newtonian ratio the paper derives from Eqs. kmf_eqn_codeunit_lin and
+    kmf_Poission_eqn_codeunit (force ratio with the mass variation)."""
+    ng = 32
+    pos, mom = _wave_load(ng, 1e-3)
+    k = _kmo_pars(beta=0.4, A_bar=1.05, bp=0.5)
+    a = 0.5
+    _, m0, _ = orc.pm_step(pos, mom, ng, ng, 0.3, a, 0.01, model=0, first=True)
+    _, m2, _ = orc.pm_step(pos, mom, ng, ng, 0.3, a, 0.01, model=2, first=True, kmo=k, box_mpch=64.0,
+                           opts=orc.Opts(rtol=1e-12, max_cycles=60))
+    K1 = 1.0 + orc.gamma_kmo(2, k["k0"], a, k["lam"]) * k["phibar_prime_over_h0"] ** 2
+    expect = k["A_bar"] * (1.0 + 2.0 * k["beta"] ** 2 / K1)
+    sel = np.abs(m0[:, 0]) > 0.5 * np.abs(m0[:, 0]).max()
+    ratio = m2[sel, 0] / m0[sel, 0]
+    assert np.allclose(ratio, expect, rtol=1e-4)
+
+
+def test_kmo_friction_on_a_uniform_load(orc):
+    """No density contrast: no force, and the momenta decay by the friction
+    factor 1 - beta (dphibar/da) da of Eq. force_Kmo2."""
+    ng = 16
+    pos, _ = _wave_load(ng, 0.0)
+    mom = np.full_like(pos, 0.25)
+    k = _kmo_pars(beta=0.3, dphibar_da=-0.8)
+    _, m2, _ = orc.pm_step(pos, mom, ng, ng, 0.3, 0.5, 0.02, model=2, kmo=k, box_mpch=64.0)
+    assert np.allclose(m2, np.float32(0.25 * (1.0 - 0.3 * (-0.8) * 0.02)), rtol=1e-6, atol=1e-7)
