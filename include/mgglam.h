@@ -261,9 +261,13 @@ int pm_newton_potential(mg_ctx *ctx, int ng, double a, double omega_m,
  * Particle-mesh state for pm_step: positions x~ (FP32, np x 3, in [0, ng))
  * at scale factor a, momenta p~ (FP32, np x 3) at a - da/2 (at a itself
  * when first != 0).  model 0 = GR (Newtonian force only), 1 = nDGP
- * (Phi = Phi_N + phi/2, Eq. poisson_nDGP).  phi_ws: ng^3 FP64 device or
- * host buffer carrying the nDGP field between steps as a warm start (may be
- * NULL; then each solve starts from zero).
+ * (Phi = Phi_N + phi/2, Eq. poisson_nDGP), 2 = Kmouflage (Eqs. force_Kmo2,
+ * kmf_Poission_eqn_codeunit: Lap Phi_N = (3/2) A Omega_m a^-1 delta,
+ * Phi = Phi_N + beta c~ phi~, and the friction term -beta (dphibar/da) p~,
+ * with the background inputs kmo (at a) and dphibar_da; the expansion is
+ * LCDM's, as for GR and nDGP).  phi_ws: ng^3 FP64 device or host buffer
+ * carrying the field between steps as a warm start (may be NULL; then each
+ * solve starts from zero).
  */
 typedef struct {
     float *pos, *mom;
@@ -274,6 +278,8 @@ typedef struct {
     int first;
     mg_dgp_params dgp;
     double *phi_ws;
+    mg_kmo_params kmo;   /* model 2: the Kmouflage parameters at a           */
+    double dphibar_da;   /* model 2: d phibar / d a at a                       */
 } pm_state;
 
 /*

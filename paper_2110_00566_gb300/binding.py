@@ -65,7 +65,8 @@ class mg_instance(C.Structure):
 class pm_state(C.Structure):
     _fields_ = [("pos", C.c_void_p), ("mom", C.c_void_p), ("np", C.c_longlong), ("ng", C.c_int),
                 ("box_mpch", C.c_double), ("omega_m", C.c_double), ("a", C.c_double), ("da", C.c_double),
-                ("model", C.c_int), ("first", C.c_int), ("dgp", mg_dgp_params), ("phi_ws", C.c_void_p)]
+                ("model", C.c_int), ("first", C.c_int), ("dgp", mg_dgp_params), ("phi_ws", C.c_void_p),
+                ("kmo", mg_kmo_params), ("dphibar_da", C.c_double)]
 
 
 class dpm_config(C.Structure):
@@ -299,13 +300,18 @@ def pm_newton_potential(ctx: Context, ng, a, omega_m, delta, phi_out):
                                              _ptr(phi_out)))
 
 
-def make_pm_state(pos, mom, ng, box_mpch, omega_m, a, da, model=1, rc_h0=1.0, first=True, phi_ws=None):
-    """A pm_state over caller arrays (kept alive by the caller)."""
+def make_pm_state(pos, mom, ng, box_mpch, omega_m, a, da, model=1, rc_h0=1.0, first=True, phi_ws=None, kmo=None):
+    """A pm_state over caller arrays (kept alive by the caller).  kmo (model
+    2): dict(n, k0, beta, lam, phibar_prime_over_h0, A_bar, dphibar_da)."""
     _check_dtype(pos, "f32")
     _check_dtype(mom, "f32")
     _check_dtype(phi_ws, "f64")
+    k = kmo or dict(n=2, k0=0.0, beta=0.0, lam=1.0, phibar_prime_over_h0=0.0, A_bar=1.0, dphibar_da=0.0)
+    kp = mg_kmo_params(int(k["n"]), float(k["k0"]), float(k["beta"]), float(k["lam"]),
+                       float(k["phibar_prime_over_h0"]), float(k["A_bar"]))
     return pm_state(_ptr(pos), _ptr(mom), int(pos.shape[0]), int(ng), float(box_mpch), float(omega_m), float(a),
-                    float(da), int(model), int(bool(first)), mg_dgp_params(float(rc_h0)), _ptr(phi_ws))
+                    float(da), int(model), int(bool(first)), mg_dgp_params(float(rc_h0)), _ptr(phi_ws), kp,
+                    float(k["dphibar_da"]))
 
 
 def pm_step(ctx: Context, state: pm_state, o: mg_opts = None):

@@ -153,6 +153,8 @@ void leave(mg_ctx *ctx);
 // nDGP solve on device arrays (validated options), and the CIC deposit
 int solve_dgp_dev(mg_ctx *ctx, int n, double a, double om, double rc, const double *delta, double *phi,
                   const mg_opts &o, mg_stats *st);
+int solve_kmo_dev(mg_ctx *ctx, const mg_grid &g, const mg_kmo_params &p, const double *delta, double *phi,
+                  const mg_opts &o, mg_stats *st);
 void cic_deposit_dev(mg_ctx *ctx, int ng, const float *pos, long long np, double *delta);
 int check_opts(mg_ctx *ctx, const mg_opts &o);
 

@@ -129,17 +129,21 @@ k_green(cufftDoubleComplex *spec, int n, const double *__restrict__ t, double sc
 
 // -grad Phi by 3-point differences at the 8 CIC cells, interpolated with the
 // CIC weights, then the leapfrog kick and drift (code units of Sec. 3.1.1):
-//   p += g ck,  x += p cd,  wrap into [0, ng).  Phi = PhiN + 0.5 phi when phi
-// is given (Eq. poisson_nDGP).  Rounded as written (no contraction).
-__device__ __forceinline__ double pot(const double *__restrict__ A, const double *__restrict__ Bp, long long q)
+//   p = p fr + g ck,  x += p cd,  wrap into [0, ng).  Phi = PhiN + cphi phi
+// when phi is given (nDGP: cphi = 1/2, Eq. poisson_nDGP; Kmouflage: cphi =
+// beta c~, Eq. force_Kmo2, whose friction term gives fr = 1 - beta
+// (dphibar/da) da_kick; fr = 1 otherwise).  Rounded as written (no
+// contraction).
+__device__ __forceinline__ double pot(const double *__restrict__ A, const double *__restrict__ Bp, double cb,
+                                      long long q)
 {
     const double a = __ldg(A + q);
-    return Bp ? __dadd_rn(a, __dmul_rn(0.5, __ldg(Bp + q))) : a;
+    return Bp ? __dadd_rn(a, __dmul_rn(cb, __ldg(Bp + q))) : a;
 }
 
 __global__ void __launch_bounds__(256)
 k_kick_drift(float *__restrict__ pos, float *__restrict__ mom, long long np, int ng, const double *__restrict__ phin,
-             const double *__restrict__ phi, double ck, double cd)
+             const double *__restrict__ phi, double cphi, double fr, double ck, double cd)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np; p += stride) {
@@ -157,16 +161,16 @@ k_kick_drift(float *__restrict__ pos, float *__restrict__ mom, long long np, int
                     const int jp = j + 1 == ng ? 0 : j + 1, jm = j == 0 ? ng - 1 : j - 1;
                     const int kp = k + 1 == ng ? 0 : k + 1, km = k == 0 ? ng - 1 : k - 1;
                     auto I3 = [ng](int x, int y, int z) { return ((long long)x * ng + y) * ng + z; };
-                    const double gx = -__dsub_rn(pot(phin, phi, I3(ip, j, k)), pot(phin, phi, I3(im, j, k))) / 2.0;
-                    const double gy = -__dsub_rn(pot(phin, phi, I3(i, jp, k)), pot(phin, phi, I3(i, jm, k))) / 2.0;
-                    const double gz = -__dsub_rn(pot(phin, phi, I3(i, j, kp)), pot(phin, phi, I3(i, j, km))) / 2.0;
+                    const double gx = -__dsub_rn(pot(phin, phi, cphi, I3(ip, j, k)), pot(phin, phi, cphi, I3(im, j, k))) / 2.0;
+                    const double gy = -__dsub_rn(pot(phin, phi, cphi, I3(i, jp, k)), pot(phin, phi, cphi, I3(i, jm, k))) / 2.0;
+                    const double gz = -__dsub_rn(pot(phin, phi, cphi, I3(i, j, kp)), pot(phin, phi, cphi, I3(i, j, km))) / 2.0;
                     g[0] = __dadd_rn(g[0], __dmul_rn(w, gx));
                     g[1] = __dadd_rn(g[1], __dmul_rn(w, gy));
                     g[2] = __dadd_rn(g[2], __dmul_rn(w, gz));
                 }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const float pn = (float)__dadd_rn((double)mom[3 * p + d], __dmul_rn(g[d], ck));
+            const float pn = (float)__dadd_rn(__dmul_rn((double)mom[3 * p + d], fr), __dmul_rn(g[d], ck));
             mom[3 * p + d] = pn;
             float x = (float)__dadd_rn((double)pos[3 * p + d], __dmul_rn((double)pn, cd));
             if (x < 0.f) x = __fadd_rn(x, (float)ng);
@@ -380,11 +384,15 @@ int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats)
 {
     if (!ctx) return MG_ERR_ARG;
     if (!st || !st->pos || !st->mom || st->np < 1) return set_err(ctx, MG_ERR_ARG, "bad pm_state");
-    if (st->model != 0 && st->model != 1) return set_err(ctx, MG_ERR_ARG, "model must be 0 (GR) or 1 (nDGP)");
-    if (st->model == 1 ? !valid_ng(st->ng) : (st->ng < 2 || st->ng % 2))
+    if (st->model < 0 || st->model > 2)
+        return set_err(ctx, MG_ERR_ARG, "model must be 0 (GR), 1 (nDGP) or 2 (Kmouflage)");
+    if (st->model >= 1 ? !valid_ng(st->ng) : (st->ng < 2 || st->ng % 2))
         return set_err(ctx, MG_ERR_ARG, "ng = %d not supported", st->ng);
     if (!(st->a > 0) || !(st->da > 0) || !(st->omega_m > 0) || (st->model == 1 && !(st->dgp.rc_h0 > 0)))
         return set_err(ctx, MG_ERR_ARG, "a, da, omega_m (and rc_h0) must be > 0");
+    if (st->model == 2 && (st->kmo.n < 2 || st->kmo.k0 < 0 || !(st->kmo.lambda > 0) || !(st->kmo.A_bar > 0) ||
+                           !(st->box_mpch > 0)))
+        return set_err(ctx, MG_ERR_ARG, "bad Kmouflage parameters");
     mg_opts o;
     if (opts)
         o = *opts;
@@ -402,9 +410,12 @@ int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats)
         pm_fft_setup(ctx, n);
         PmWork &w = pmw(ctx);
         cic_deposit_dev(ctx, n, dpos, st->np, w.rho);
-        newton_potential_dev(ctx, n, st->a, st->omega_m, w.rho, w.phin);
+        // Kmouflage: Lap Phi_N = (3/2) A Omega_m a^-1 delta (Eq. kmf_Poission_eqn_codeunit)
+        const double Af = st->model == 2 ? st->kmo.A_bar : 1.0;
+        newton_potential_dev(ctx, n, st->a, st->omega_m * Af, w.rho, w.phin);
         const double *dphi = nullptr;
-        if (st->model == 1) {
+        double cphi = 0.5, fr = 1.0;
+        if (st->model >= 1) {
             double *phib = w.phi;
             if (st->phi_ws) {
                 phib = (double *)stage_in(ctx, 2, st->phi_ws, cb, true);
@@ -412,7 +423,14 @@ int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats)
             } else {
                 o.warm_start = 0;
             }
-            rc = solve_dgp_dev(ctx, n, st->a, st->omega_m, st->dgp.rc_h0, w.rho, phib, o, &loc);
+            if (st->model == 1) {
+                rc = solve_dgp_dev(ctx, n, st->a, st->omega_m, st->dgp.rc_h0, w.rho, phib, o, &loc);
+            } else {
+                const mg_grid g{n, st->box_mpch, st->a, st->omega_m};
+                rc = solve_kmo_dev(ctx, g, st->kmo, w.rho, phib, o, &loc);
+                cphi = st->kmo.beta_kmo * 2997.92458 * n / st->box_mpch;   // beta c~
+                fr = 1.0 - st->kmo.beta_kmo * st->dphibar_da * (st->first ? 0.5 * st->da : st->da);
+            }
             if (rc < 0) {
                 leave(ctx);
                 if (stats) *stats = loc;
@@ -426,7 +444,7 @@ int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats)
         const double ck = dak / (a * E_lcdm(a, om));
         const double am = a + 0.5 * da;
         const double cd = da / (std::pow(am, 3.0) * E_lcdm(am, om));
-        k_kick_drift<<<grid1(st->np), 256, 0, ctx->stream>>>(dpos, dmom, st->np, n, w.phin, dphi, ck, cd);
+        k_kick_drift<<<grid1(st->np), 256, 0, ctx->stream>>>(dpos, dmom, st->np, n, w.phin, dphi, cphi, fr, ck, cd);
         MG_CK(cudaGetLastError());
         stage_out(ctx, st->pos, dpos, pb);
         stage_out(ctx, st->mom, dmom, pb);

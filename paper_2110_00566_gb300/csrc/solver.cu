@@ -663,6 +663,27 @@ static int solve_any(mg_ctx *ctx, int n, const ModelDesc &md, const double *delt
     return rc;
 }
 
+// Kmouflage operator description (the model's constants in code units)
+static ModelDesc kmo_desc(const mg_grid &g, const mg_kmo_params &p)
+{
+    const double a = g.a;
+    double gam = p.n * p.k0;
+    for (int q = 0; q < p.n - 1; ++q) gam *= 1.0 / (2.0 * a * a * p.lambda * p.lambda);
+    const double ct = 2997.92458 * g.ng / g.box_mpch;   // c~ = (c/H0) N / L
+    const double coef = 3.0 * p.beta_kmo * p.A_bar * g.omega_m / a / ct;
+    const double b = p.phibar_prime_over_h0 * p.phibar_prime_over_h0;
+    return ModelDesc{1, 0.0, p.n, gam, b, coef, coef};
+}
+
+// Kmouflage solve on device arrays (used by the particle-mesh step)
+int solve_kmo_dev(mg_ctx *ctx, const mg_grid &g, const mg_kmo_params &p, const double *delta, double *phi,
+                  const mg_opts &o, mg_stats *st)
+{
+    const ModelDesc md = kmo_desc(g, p);
+    if (o.precision == MG_PREC_FP64) return solve_plain<double>(ctx, g.ng, md, delta, phi, o, st);
+    return solve_mixed(ctx, g.ng, md, delta, phi, o, st);
+}
+
 // nDGP solve on device arrays (used by the particle-mesh step)
 int solve_dgp_dev(mg_ctx *ctx, int n, double a, double om, double rc, const double *delta, double *phi,
                   const mg_opts &o, mg_stats *st)
@@ -855,14 +876,7 @@ int mg_solve_kmouflage(mg_ctx *ctx, const mg_grid *g, const mg_kmo_params *p, co
     if (rc) return rc;
     try {
         enter(ctx);
-        const double a = g->a;
-        double gam = p->n * p->k0;
-        for (int q = 0; q < p->n - 1; ++q) gam *= 1.0 / (2.0 * a * a * p->lambda * p->lambda);
-        const double ct = 2997.92458 * g->ng / g->box_mpch;   // c~ = (c/H0) N / L
-        const double coef = 3.0 * p->beta_kmo * p->A_bar * g->omega_m / a / ct;
-        const double b = p->phibar_prime_over_h0 * p->phibar_prime_over_h0;
-        ModelDesc md{1, 0.0, p->n, gam, b, coef, coef};
-        rc = solve_any(ctx, g->ng, md, delta, phi, o, stats);
+        rc = solve_any(ctx, g->ng, kmo_desc(*g, *p), delta, phi, o, stats);
         leave(ctx);
     } catch (CudaFail &f) {
         return f.code;

@@ -32,23 +32,28 @@ def _load(ng, nps, seed, a):
     return inputs.zeldovich(nps, ng, 2.0 * ng, pk, D, seed=seed, vel_factor=vel * D)
 
 
-@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("model", [0, 1, 2])
 def test_pm_steps_match_oracle(B, ctx, model):
-    """Five leapfrog steps from a = 0.1 (the first a half kick), GR and
-    nDGP (H0 r_c = 1), 16^3 particles on a 32^3 mesh."""
+    """Five leapfrog steps from a = 0.1 (the first a half kick), GR, nDGP
+    (H0 r_c = 1) and Kmouflage (n = 2, K0 = 1, beta = 0.2, with background
+    inputs phibar'/H0 = -1e-3, A = exp(-0.02), dphibar/da = 0.05), 16^3
+    particles on a 32^3 mesh."""
     ng, nps, a0, da = 32, 16, 0.1, 0.05
     pos, mom = _load(ng, nps, 7, a0)
     p_ref, m_ref = pos.copy(), mom.copy()
     p_gpu, m_gpu = pos.copy(), mom.copy()
     phi_ref = None
     phi_ws = np.zeros((ng,) * 3)
+    kmo = dict(n=2, k0=1.0, beta=0.2, lam=float(np.sqrt(2.1)), phibar_prime_over_h0=-1e-3,
+               A_bar=float(np.exp(-0.02)), dphibar_da=0.05)
     st = B.make_pm_state(p_gpu, m_gpu, ng, 2.0 * ng, 0.3, a0, da, model=model, rc_h0=1.0, first=True,
-                         phi_ws=phi_ws if model else None)
+                         phi_ws=phi_ws if model else None, kmo=kmo if model == 2 else None)
     a = a0
     o = B.opts(rtol=1e-12, max_cycles=40)
     for s in range(5):
         p_ref, m_ref, phi_ref = oracle.pm_step(p_ref, m_ref, ng, nps, 0.3, a, da, model, 1.0, first=(s == 0),
-                                               phi_guess=phi_ref, opts=oracle.Opts(rtol=1e-12, max_cycles=40))
+                                               phi_guess=phi_ref, opts=oracle.Opts(rtol=1e-12, max_cycles=40),
+                                               kmo=kmo if model == 2 else None, box_mpch=2.0 * ng)
         B.pm_step(ctx, st, o)
         a += da
     assert st.a == pytest.approx(a) and st.first == 0
@@ -58,7 +63,11 @@ def test_pm_steps_match_oracle(B, ctx, model):
     assert dp.max() <= 4 * ulp, dp.max()
     assert np.abs(m_gpu - m_ref).max() <= 1e-5 * np.abs(m_ref).max()
     if model:
-        assert np.abs(phi_ws - phi_ref).max() < 1e-8 * np.abs(phi_ref).max()
+        # both fields solved to a 1e-12 relative residual; the Kmouflage
+        # field's smoother source (rms delta / c~ ~ 1e-5) leaves it less
+        # well conditioned relative to its own size
+        tol = 1e-8 if model == 1 else 1e-7
+        assert np.abs(phi_ws - phi_ref).max() < tol * np.abs(phi_ref).max()
 
 
 def test_pm_momentum_conserved(B, ctx):
