@@ -89,9 +89,9 @@ typedef struct {
 } mg_dgp_params;
 
 /* Kmouflage, K(X) = -1 + X + K0 X^n, A = exp(beta phi) (Sec. 2.2, 3.2.4):
- * gamma = n K0 (1/(2 a^2 lambda^2))^(n-1) is derived; the background
- * phibar'/H0 and A(phibar) are inputs (the background solver is not part
- * of this library). */
+ * gamma = n K0 (1/(2 a^2 lambda^2))^(n-1) is derived; lambda, the
+ * background phibar'/H0 and A(phibar) are inputs, which
+ * mg_kmo_background computes. */
 typedef struct {
     int n;                        /* exponent, n >= 2                          */
     double k0;                    /* K0 >= 0                                   */
@@ -100,6 +100,52 @@ typedef struct {
     double phibar_prime_over_h0;  /* phibar' / H0 (conformal-time derivative)  */
     double A_bar;                 /* A(phibar)                                 */
 } mg_kmo_params;
+
+/* ---- Kmouflage background (Sec. 3.2.4, background solver) ------------- */
+
+/* Model and cosmology of the background solve.  Omega_r is that of photons
+ * at t_cmb plus n_eff massless neutrino species (Omega_gamma from the
+ * black-body density over 3 (100 h km/s/Mpc)^2 / (8 pi G)). */
+typedef struct {
+    int n;              /* K(X) = -1 + X + K0 X^n, n >= 2                      */
+    double k0;          /* K0 >= 0                                            */
+    double beta_kmo;    /* A(phi) = exp(beta phi)                             */
+    double omega_m, h;  /* Omega_m; H0 = 100 h km/s/Mpc                       */
+    double t_cmb;       /* K (0: no radiation)                                */
+    double n_eff;       /* massless neutrino species                          */
+    double a_ini;       /* start of the integration, 0 < a_ini < 1            */
+    double phi_ini;     /* phibar at a_ini                                    */
+    double dphi_ini;    /* d phibar / d ln a at a_ini                         */
+    double rtol;        /* local relative error per step of the integrator    */
+    double h0_tol;      /* |H(a=1)/H0 - 1| accepted by the lambda shooting    */
+} mg_kmo_background_params;
+
+/* Defaults: n = 2, K0 = 1, beta = 0.2, Omega_m = 0.3089, h = 0.6774,
+ * t_cmb = 2.7255, n_eff = 3.046, a_ini = 1e-5 (z = 1e5), phi_ini =
+ * dphi_ini = 1e-30, rtol = 1e-12, h0_tol = 1e-12.  Errors: MG_ERR_ARG. */
+int mg_kmo_background_defaults(mg_kmo_background_params *p);
+
+/*
+ * HOST.  The background of the Kmouflage model: the field equation (Eq.
+ * kmf_background_eom2) integrated in N = ln a from a_ini with an adaptive
+ * Dormand-Prince 5(4) Runge-Kutta pair, the conformal Hubble rate at each
+ * point taken from the Friedmann equation (Eq. kmf_background_Friedmann,
+ * a polynomial in (H/H0)^2 solved by Newton's method on its LCDM-connected
+ * branch) and its derivative from the acceleration equation a''/a =
+ * -(4 pi G/3)(rho + 3p) with the scalar's energy density and pressure.
+ * lambda: if lambda_in > 0 it is used as given; otherwise it is found by
+ * shooting (Illinois regula falsi) so that H(a = 1) = H0 to h0_tol.
+ * a: na > 0 host scale factors, each in [a_ini, 100], any order.
+ * out: host, na x 5 doubles, row i for a[i]:
+ *   [H/H0, phibar, d phibar / d a, A(phibar), phibar'/H0]
+ * (phibar' the conformal-time derivative: the mg_kmo_params input).
+ * lambda_out: host scalar (may be NULL).
+ * Returns MG_OK, MG_WARN_NOT_CONVERGED (the shooting did not reach h0_tol;
+ * the table is that of the last lambda), MG_ERR_ARG or MG_ERR_NONFINITE
+ * (the Friedmann equation lost its real root, or the integrator failed).
+ */
+int mg_kmo_background(const mg_kmo_background_params *p, double lambda_in, int na,
+                      const double *a, double *out, double *lambda_out);
 
 /* ---- solver options ---------------------------------------------------- */
 #define MG_CYCLE_V 0
@@ -264,8 +310,9 @@ int pm_newton_potential(mg_ctx *ctx, int ng, double a, double omega_m,
  * (Phi = Phi_N + phi/2, Eq. poisson_nDGP), 2 = Kmouflage (Eqs. force_Kmo2,
  * kmf_Poission_eqn_codeunit: Lap Phi_N = (3/2) A Omega_m a^-1 delta,
  * Phi = Phi_N + beta c~ phi~, and the friction term -beta (dphibar/da) p~,
- * with the background inputs kmo (at a) and dphibar_da; the expansion is
- * LCDM's, as for GR and nDGP).  phi_ws: ng^3 FP64 device or host buffer
+ * with the background inputs kmo (at a) and dphibar_da).  The expansion
+ * rate is e_a, e_mid when both are set (the Kmouflage background of
+ * mg_kmo_background), else LCDM's.  phi_ws: ng^3 FP64 device or host buffer
  * carrying the field between steps as a warm start (may be NULL; then each
  * solve starts from zero).
  */
@@ -280,6 +327,8 @@ typedef struct {
     double *phi_ws;
     mg_kmo_params kmo;   /* model 2: the Kmouflage parameters at a           */
     double dphibar_da;   /* model 2: d phibar / d a at a                       */
+    double e_a, e_mid;   /* H/H0 at a and at a + da/2 for the kick and drift;
+                            0 (either) = LCDM's from omega_m                   */
 } pm_state;
 
 /*
@@ -288,7 +337,8 @@ typedef struct {
  * Lap Phi_N = (3/2) Omega_m a^-1 delta with the 7-point Green's function,
  * the nDGP field (model 1), 3-point gradient of Phi at the 8 CIC cells
  * interpolated to each particle, kick p += g da/(a E(a)) (da/2 if first),
- * drift x += p da/(a_m^3 E(a_m)) with a_m = a + da/2, wrap into [0, ng).
+ * drift x += p da/(a_m^3 E(a_m)) with a_m = a + da/2, wrap into [0, ng);
+ * E = H/H0 (e_a, e_mid when set).
  * Updates pos, mom, a (+= da) and first (= 0).  stats: the nDGP solve.
  */
 int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats);

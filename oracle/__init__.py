@@ -348,7 +348,7 @@ def _wrap32(x, ng):
 
 
 def pm_step(pos, mom, ng, np_side, omega_m, a, da, model=1, rc_h0=1.0, first=False,
-            phi_guess=None, opts: Opts = None, kmo=None, box_mpch=None):
+            phi_guess=None, opts: Opts = None, kmo=None, box_mpch=None, hubble=None):
     """One leapfrog step in the scale factor (Sec. 3.1.1 code-unit equations
     of motion, with the drift sign of Eq. force_Kmo1):
         dp~/da = -(H0/adot) grad~ Phi~,   dx~/da = H0/(a^2 adot) p~,
@@ -360,7 +360,9 @@ def pm_step(pos, mom, ng, np_side, omega_m, a, da, model=1, rc_h0=1.0, first=Fal
     field, and the friction term dp~/da = -beta (dphibar/da) p~ taken in the
     kick as the factor 1 - beta (dphibar/da) da_kick; kmo = dict(n, k0, beta,
     lam, phibar_prime_over_h0, A_bar, dphibar_da), the background inputs at
-    a, and box_mpch the box (for c~).  FP32 state, FP64 force.
+    a, and box_mpch the box (for c~).  hubble = (E(a), E(a + da/2)), the
+    model's own H/H0 (the Kmouflage background), replaces LCDM's E in
+    H0/adot = 1/(a E).  FP32 state, FP64 force.
     Returns (pos, mom, phi)."""
     delta, _ = cic_deposit(pos, ng, np_side)
     phi = None
@@ -379,9 +381,10 @@ def pm_step(pos, mom, ng, np_side, omega_m, a, da, model=1, rc_h0=1.0, first=Fal
         phi, _ = dgp_solve(delta, a, omega_m, rc_h0, opts, phi_guess)
         phin = phin + 0.5 * phi
     acc = cic_force(phin, pos)
-    mom = (mom.astype(np.float64) * fr + acc * (dak / (a * E_lcdm(a, omega_m)))).astype(np.float32)
     am = a + 0.5 * da
-    pos = (pos.astype(np.float64) + mom.astype(np.float64) * (da / (am ** 3 * E_lcdm(am, omega_m))))
+    E_a, E_m = hubble if hubble is not None else (E_lcdm(a, omega_m), E_lcdm(am, omega_m))
+    mom = (mom.astype(np.float64) * fr + acc * (dak / (a * E_a))).astype(np.float32)
+    pos = (pos.astype(np.float64) + mom.astype(np.float64) * (da / (am ** 3 * E_m)))
     return _wrap32(pos, ng), mom, phi
 
 

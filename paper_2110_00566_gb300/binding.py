@@ -66,7 +66,14 @@ class pm_state(C.Structure):
     _fields_ = [("pos", C.c_void_p), ("mom", C.c_void_p), ("np", C.c_longlong), ("ng", C.c_int),
                 ("box_mpch", C.c_double), ("omega_m", C.c_double), ("a", C.c_double), ("da", C.c_double),
                 ("model", C.c_int), ("first", C.c_int), ("dgp", mg_dgp_params), ("phi_ws", C.c_void_p),
-                ("kmo", mg_kmo_params), ("dphibar_da", C.c_double)]
+                ("kmo", mg_kmo_params), ("dphibar_da", C.c_double), ("e_a", C.c_double),
+                ("e_mid", C.c_double)]
+
+
+class mg_kmo_background_params(C.Structure):
+    _fields_ = [("n", C.c_int), ("k0", C.c_double), ("beta_kmo", C.c_double), ("omega_m", C.c_double),
+                ("h", C.c_double), ("t_cmb", C.c_double), ("n_eff", C.c_double), ("a_ini", C.c_double),
+                ("phi_ini", C.c_double), ("dphi_ini", C.c_double), ("rtol", C.c_double), ("h0_tol", C.c_double)]
 
 
 class dpm_config(C.Structure):
@@ -102,6 +109,9 @@ def _declare(L):
         "pm_cic_index": (C.c_int, [_VP, C.c_int, _VP, C.c_longlong, _VP]),
         "pm_cic_deposit_noalloc": (C.c_int, [C.c_int, _VP, C.c_longlong, _VP, _VP]),
         "pm_step": (C.c_int, [_VP, _P(pm_state), _P(mg_opts), _P(mg_stats)]),
+        "mg_kmo_background_defaults": (C.c_int, [_P(mg_kmo_background_params)]),
+        "mg_kmo_background": (C.c_int, [_P(mg_kmo_background_params), C.c_double, C.c_int, _VP, _VP,
+                                        _P(C.c_double)]),
         "pm_newton_potential": (C.c_int, [_VP, C.c_int, C.c_double, C.c_double, _VP, _VP]),
         "mg_solve_adjoint": (C.c_int, [_VP, _P(mg_grid), _P(mg_dgp_params), _P(mg_opts), _VP, _VP, _VP, _VP,
                                        _VP, _P(mg_stats)]),
@@ -300,9 +310,11 @@ def pm_newton_potential(ctx: Context, ng, a, omega_m, delta, phi_out):
                                              _ptr(phi_out)))
 
 
-def make_pm_state(pos, mom, ng, box_mpch, omega_m, a, da, model=1, rc_h0=1.0, first=True, phi_ws=None, kmo=None):
+def make_pm_state(pos, mom, ng, box_mpch, omega_m, a, da, model=1, rc_h0=1.0, first=True, phi_ws=None, kmo=None,
+                  hubble=None):
     """A pm_state over caller arrays (kept alive by the caller).  kmo (model
-    2): dict(n, k0, beta, lam, phibar_prime_over_h0, A_bar, dphibar_da)."""
+    2): dict(n, k0, beta, lam, phibar_prime_over_h0, A_bar, dphibar_da).
+    hubble: (H/H0 at a, H/H0 at a + da/2), or None for LCDM's."""
     _check_dtype(pos, "f32")
     _check_dtype(mom, "f32")
     _check_dtype(phi_ws, "f64")
@@ -311,7 +323,35 @@ def make_pm_state(pos, mom, ng, box_mpch, omega_m, a, da, model=1, rc_h0=1.0, fi
                        float(k["phibar_prime_over_h0"]), float(k["A_bar"]))
     return pm_state(_ptr(pos), _ptr(mom), int(pos.shape[0]), int(ng), float(box_mpch), float(omega_m), float(a),
                     float(da), int(model), int(bool(first)), mg_dgp_params(float(rc_h0)), _ptr(phi_ws), kp,
-                    float(k["dphibar_da"]))
+                    float(k["dphibar_da"]), *(float(e) for e in (hubble or (0.0, 0.0))))
+
+
+def kmo_background_params(**kw):
+    """mg_kmo_background_params with the library defaults, overridden by kw
+    (n, k0, beta_kmo, omega_m, h, t_cmb, n_eff, a_ini, phi_ini, dphi_ini,
+    rtol, h0_tol)."""
+    p = mg_kmo_background_params()
+    lib().mg_kmo_background_defaults(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError("unknown background parameter %r" % k)
+        setattr(p, k, v)
+    return p
+
+
+def mg_kmo_background(p: mg_kmo_background_params, a, lam=0.0):
+    """Kmouflage background at the scale factors a (host code in the
+    library): returns (rc, lambda, table (len(a), 5) of [H/H0, phibar,
+    dphibar/da, A(phibar), phibar'/H0]).  lam > 0 skips the shooting."""
+    a = np.ascontiguousarray(np.atleast_1d(np.asarray(a, dtype=np.float64)))
+    out = np.empty((a.size, 5))
+    lam_out = C.c_double(0.0)
+    rc = lib().mg_kmo_background(C.byref(p), float(lam), int(a.size), a.ctypes.data, out.ctypes.data,
+                                 C.byref(lam_out))
+    if rc < 0:
+        raise MGError(rc, "mg_kmo_background: bad argument" if rc == MG_ERR_ARG else
+                      "mg_kmo_background: the Friedmann equation lost its root or the integration failed")
+    return rc, lam_out.value, out
 
 
 def pm_step(ctx: Context, state: pm_state, o: mg_opts = None):

@@ -393,6 +393,8 @@ int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats)
     if (st->model == 2 && (st->kmo.n < 2 || st->kmo.k0 < 0 || !(st->kmo.lambda > 0) || !(st->kmo.A_bar > 0) ||
                            !(st->box_mpch > 0)))
         return set_err(ctx, MG_ERR_ARG, "bad Kmouflage parameters");
+    if (!(st->e_a >= 0.0) || !(st->e_mid >= 0.0) || !std::isfinite(st->e_a) || !std::isfinite(st->e_mid))
+        return set_err(ctx, MG_ERR_ARG, "e_a, e_mid must be finite and >= 0");
     mg_opts o;
     if (opts)
         o = *opts;
@@ -441,9 +443,10 @@ int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats)
         }
         const double a = st->a, da = st->da, om = st->omega_m;
         const double dak = st->first ? 0.5 * da : da;
-        const double ck = dak / (a * E_lcdm(a, om));
         const double am = a + 0.5 * da;
-        const double cd = da / (std::pow(am, 3.0) * E_lcdm(am, om));
+        const bool own_e = st->e_a > 0.0 && st->e_mid > 0.0;   // the caller's expansion history
+        const double ck = dak / (a * (own_e ? st->e_a : E_lcdm(a, om)));
+        const double cd = da / (std::pow(am, 3.0) * (own_e ? st->e_mid : E_lcdm(am, om)));
         k_kick_drift<<<grid1(st->np), 256, 0, ctx->stream>>>(dpos, dmom, st->np, n, w.phin, dphi, cphi, fr, ck, cd);
         MG_CK(cudaGetLastError());
         stage_out(ctx, st->pos, dpos, pb);

@@ -81,3 +81,50 @@ def test_pm_momentum_conserved(B, ctx):
     B.pm_step(ctx, st, B.opts())
     tot = mom.astype(np.float64).sum(axis=0)
     assert np.abs(tot).max() < 1e-5 * np.abs(mom).sum()
+
+
+def test_kmouflage_pm_on_its_own_background(B, ctx):
+    """Five Kmouflage steps from a = 0.3 driven by the background solve
+    (n = 2, K0 = 1, beta = 0.2): lambda, phibar'/H0, A(phibar), dphibar/da
+    and the expansion rate at a and a + da/2 from the library's background
+    solver on the GPU side and from the oracle's on the oracle side."""
+    from oracle import background as ob
+    ng, nps, a0, da, om = 32, 16, 0.3, 0.05, 0.3089
+    pos, mom = _load(ng, nps, 11, a0)
+    p_ref, m_ref = pos.copy(), mom.copy()
+    p_gpu, m_gpu = pos.copy(), mom.copy()
+    steps = [a0 + s * da for s in range(5)]
+    a_all = sorted(steps + [x + 0.5 * da for x in steps])
+    bp = B.kmo_background_params(n=2, k0=1.0, beta_kmo=0.2, omega_m=om)
+    _, lam_g, tab_g = B.mg_kmo_background(bp, a_all)
+    lam_o, tab_o = ob.solve(ob.Background(n=2, k0=1.0, beta=0.2, omega_m=om), a_all)
+    row = {round(x, 12): i for i, x in enumerate(a_all)}
+
+    def inputs_at(tab, lam, a):
+        r, m = tab[row[round(a, 12)]], tab[row[round(a + 0.5 * da, 12)]]
+        kmo = dict(n=2, k0=1.0, beta=0.2, lam=lam, phibar_prime_over_h0=r[4], A_bar=r[3], dphibar_da=r[2])
+        return kmo, (r[0], m[0])
+
+    phi_ws = np.zeros((ng,) * 3)
+    kmo, hub = inputs_at(tab_g, lam_g, a0)
+    st = B.make_pm_state(p_gpu, m_gpu, ng, 2.0 * ng, om, a0, da, model=2, first=True, phi_ws=phi_ws, kmo=kmo,
+                         hubble=hub)
+    o = B.opts(rtol=1e-12, max_cycles=40)
+    phi_ref = None
+    for s, a in enumerate(steps):
+        kmo_o, hub_o = inputs_at(tab_o, lam_o, a)
+        p_ref, m_ref, phi_ref = oracle.pm_step(p_ref, m_ref, ng, nps, om, a, da, 2, first=(s == 0),
+                                               phi_guess=phi_ref, opts=oracle.Opts(rtol=1e-12, max_cycles=40),
+                                               kmo=kmo_o, box_mpch=2.0 * ng, hubble=hub_o)
+        kmo, hub = inputs_at(tab_g, lam_g, a)
+        st.kmo.lambda_, st.kmo.phibar_prime_over_h0, st.kmo.A_bar = kmo["lam"], kmo["phibar_prime_over_h0"], \
+            kmo["A_bar"]
+        st.dphibar_da, st.e_a, st.e_mid = kmo["dphibar_da"], hub[0], hub[1]
+        B.pm_step(ctx, st, o)
+    assert hub_o[0] != pytest.approx(oracle.E_lcdm(steps[-1], om), rel=1e-4)   # the history is not LCDM's
+    ulp = np.spacing(np.float32(ng))
+    dp = np.abs(p_gpu.astype(np.float64) - p_ref.astype(np.float64))
+    dp = np.minimum(dp, ng - dp)
+    assert dp.max() <= 4 * ulp, dp.max()
+    assert np.abs(m_gpu - m_ref).max() <= 1e-5 * np.abs(m_ref).max()
+    assert np.abs(phi_ws - phi_ref).max() < 1e-7 * np.abs(phi_ref).max()
