@@ -58,6 +58,8 @@ def args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-forms", action="store_true")
     p.add_argument("--inner", type=int, default=0, help="FP32 cycles per FP64 defect (0: library default)")
+    p.add_argument("--fp32-smoother", type=int, default=0,
+                   help="FP32 half-sweep kernel: 0 autotuned, -1 gathering, k >= 1 streaming variant k")
     p.add_argument("--batch", type=int, default=64, help="instances of the batched form (0: skip)")
     p.add_argument("--adj-ng", type=int, default=128, help="mesh of the adjoint form (0: skip)")
     p.add_argument("--pm-adj-ng", type=int, default=128,
@@ -219,6 +221,8 @@ def main():
     from paper_2110_00566_gb300 import binding as B
 
     ctx = B.Context(local, torch.cuda.current_stream(dev))
+    if a.fp32_smoother:
+        ctx.set_fp32_smoother(a.fp32_smoother)
     ng = a.ng
     pos = torch.from_numpy(particles(a, rank)).to(dev)
     delta = torch.empty((ng, ng, ng), dtype=torch.float64, device=dev)

@@ -66,6 +66,17 @@ long long mg_ctx_workspace_bytes(const mg_ctx *ctx);
  * MG_OK or MG_ERR_ARG (ctx == NULL). */
 int mg_ctx_set_profiling(mg_ctx *ctx, int on);
 
+/* Choice of the FP32 half-sweep kernel on the 256^3 and 512^3 levels of the
+ * mixed-precision solve: 0 (default) = autotuned per level on first use
+ * between the gathering kernel (rows read through L1/L2) and the streaming
+ * kernel (planes staged in shared memory by bulk asynchronous copies);
+ * -1 = gathering kernel only; k >= 1 = streaming variant k (ring depth and
+ * planes per block; at most mg_fp32_smoother_variants()).  Both kernels
+ * give bit-identical fields.  Resets the tuning and the cached cycle graphs.
+ * Errors: MG_ERR_ARG. */
+int mg_ctx_set_fp32_smoother(mg_ctx *ctx, int choice);
+int mg_fp32_smoother_variants(void);
+
 /* Measured FP64 and FP32 fused multiply-add throughput of the context's
  * device in TFLOP/s (an FMA counts 2), from eight independent FMA chains
  * per thread on 16 CTAs per SM: the denominator for kernels bound by plain

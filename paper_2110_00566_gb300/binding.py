@@ -99,6 +99,8 @@ def _declare(L):
         "mg_last_error_string": (C.c_char_p, [_VP]),
         "mg_ctx_workspace_bytes": (C.c_longlong, [_VP]),
         "mg_ctx_set_profiling": (C.c_int, [_VP, C.c_int]),
+        "mg_ctx_set_fp32_smoother": (C.c_int, [_VP, C.c_int]),
+        "mg_fp32_smoother_variants": (C.c_int, []),
         "mg_probe_alu_peaks": (C.c_int, [_VP, _P(C.c_double), _P(C.c_double)]),
         "mg_opts_default": (None, [_P(mg_opts)]),
         "mg_solve_dgp": (C.c_int, [_VP, C.c_int, _P(mg_instance), _P(mg_opts), _P(mg_stats)]),
@@ -230,6 +232,10 @@ class Context:
     def set_profiling(self, on: bool):
         return self._rc(lib().mg_ctx_set_profiling(self.h, int(bool(on))))
 
+    def set_fp32_smoother(self, choice: int):
+        """-1 gathering kernel, 0 autotuned, k >= 1 streaming variant k."""
+        return self._rc(lib().mg_ctx_set_fp32_smoother(self.h, int(choice)))
+
     def probe_alu_peaks(self):
         """(FP64, FP32) FMA throughput in TFLOP/s measured on this device."""
         a, b = C.c_double(), C.c_double()
@@ -337,6 +343,10 @@ def kmo_background_params(**kw):
             raise TypeError("unknown background parameter %r" % k)
         setattr(p, k, v)
     return p
+
+
+def fp32_smoother_variants() -> int:
+    return int(lib().mg_fp32_smoother_variants())
 
 
 def mg_kmo_background(p: mg_kmo_background_params, a, lam=0.0):

@@ -120,6 +120,7 @@ struct mg_ctx {
     std::map<int, int> tuned_tx;     // autotuned tile width per level size
     // profiling of the finest-level smoother (events recorded in the graphs)
     int prof_on = 0;
+    int fp32_smoother = 0;           // -1 gathering kernel, 0 autotuned, k > 0 streaming variant k
     int prof_k = 0;                  // launches bracketed in the current cycle
     std::vector<cudaEvent_t> pev;    // pairs (start, stop)
 };

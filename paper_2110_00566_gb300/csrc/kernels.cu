@@ -140,6 +140,7 @@ template <>
 bool launch_smooth4<float>(const LevArrays<float> &L, const LevK<float> &K, const OpK<float> *op, int colour, int nb,
                            cudaStream_t st)
 {
+    if (L.qstream > 0 && launch_smooth_stream(L, K, op, colour, nb, L.qstream, st)) return true;
     return launch_smooth4_bx(L, K, op, colour, nb, L.qbx, st);
 }
 

@@ -24,6 +24,7 @@ struct LevArrays {
     LevScal *sc;         // this level's device scalars
     int model = -1;      // operator of the uploaded OpK (0 nDGP, 1 Kmouflage), -1 unknown
     int qbx = 0;         // FP32 four-cell smoother: threads along a row (autotuned; 0 = default)
+    int qstream = 0;     // FP32 streaming smoother variant (autotuned; <= 0: the gathering kernel)
     T *U(int colour) const { return u[cur[colour]][colour]; }
 };
 
@@ -38,6 +39,17 @@ void launch_smooth_shape(const LevArrays<T> &L, const OpK<T> *op, int colour, in
 // the alternate buffer, leaving the buffer state untouched (autotuner);
 // false when the level does not use the four-cell kernel
 bool launch_smooth4_shape(const LevArrays<float> &L, const OpK<float> *op, int colour, int bx, cudaStream_t st);
+// streaming FP32 four-cell half-sweep (shared-memory plane ring fed by bulk
+// asynchronous copies) for n = 256 and 512: variants 1 .. stream_variants()
+// (ring depth and planes per block); false when the level is not eligible
+int stream_variants();
+void stream_setup();   // shared-memory limits of the streaming kernels (once)
+bool stream_eligible(const LevArrays<float> &L);
+bool launch_smooth_stream(const LevArrays<float> &L, const LevK<float> &K, const OpK<float> *op, int colour, int nb,
+                          int variant, cudaStream_t st);
+// the streaming kernel's timeout flag (1 if a bounded wait gave up since the
+// last reset, -1 on a CUDA error); synchronises the stream
+int stream_timeout_flag(cudaStream_t st, bool reset);
 // residual norm; with D set also writes -d (with the old c) as FP32,
 // colour-split
 template <typename T>

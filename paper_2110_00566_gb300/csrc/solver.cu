@@ -8,6 +8,8 @@
 
 #include "ctx.cuh"
 
+#include <functional>
+
 namespace mg {
 
 // ---------------------------------------------------------------------------
@@ -472,6 +474,26 @@ static int solve_plain(mg_ctx *ctx, int n, const ModelDesc &md, const double *de
 // 8, 16, 32 or 64; 256 per block), picked once per pyramid by timing
 // half-sweeps on the level's own arrays (into the alternate buffer) before
 // any cycle is captured.  Levels below 64^3 keep the default.
+static float time_launch(mg_ctx *ctx, const std::function<bool(int)> &launch)
+{
+    cudaStream_t s = ctx->stream;
+    float t = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+        MG_CK(cudaEventRecord(ctx->t0, s));
+        if (!launch(r & 1)) return 1e30f;
+        MG_CK(cudaEventRecord(ctx->t1, s));
+        MG_CK(cudaEventSynchronize(ctx->t1));
+        float ms = 0.f;
+        MG_CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
+        t = std::min(t, ms);
+    }
+    MG_CK(cudaGetLastError());
+    return t;
+}
+
+// per FP32 level: the gathering kernel's block shape, and whether a
+// streaming variant beats it (each candidate timed on both colours into the
+// alternate buffers, so the level's state is untouched)
 static void tune_smooth4(mg_ctx *ctx, Pyramid<float> &P)
 {
     cudaStream_t s = ctx->stream;
@@ -482,23 +504,30 @@ static void tune_smooth4(mg_ctx *ctx, Pyramid<float> &P)
         for (int bx : {8, 16, 32, 64}) {
             if (bx > L.half / 4) continue;
             if (!launch_smooth4_shape(L, P.opT, 0, bx, s)) break;
-            float t = 1e30f;
-            for (int r = 0; r < 3; ++r) {
-                MG_CK(cudaEventRecord(ctx->t0, s));
-                launch_smooth4_shape(L, P.opT, r & 1, bx, s);
-                MG_CK(cudaEventRecord(ctx->t1, s));
-                MG_CK(cudaEventSynchronize(ctx->t1));
-                float ms = 0.f;
-                MG_CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
-                t = std::min(t, ms);
-            }
-            MG_CK(cudaGetLastError());
+            const float t = time_launch(ctx, [&](int c) { return launch_smooth4_shape(L, P.opT, c, bx, s); });
             if (t < best_ms) {
                 best_ms = t;
                 best = bx;
             }
         }
         L.qbx = best > 0 ? best : -1;
+        L.qstream = -1;
+        if (!stream_eligible(L) || ctx->fp32_smoother < 0) continue;
+        if (ctx->fp32_smoother > 0) {
+            stream_setup();
+            L.qstream = ctx->fp32_smoother;
+            continue;
+        }
+        const LevK<float> K = make_levk<float>(L.n, L.h);
+        for (int v = 1; v <= stream_variants(); ++v) {
+            const float t = time_launch(ctx, [&](int c) {
+                return launch_smooth_stream(L, K, P.opT, c, 1 - L.cur[c], v, s);
+            });
+            if (t < best_ms) {
+                best_ms = t;
+                L.qstream = v;
+            }
+        }
     }
 }
 
@@ -608,6 +637,17 @@ int solve_mixed(mg_ctx *ctx, int n, const ModelDesc &md, const double *delta, do
         if (ran > 0 && eps > 0 && eps < eps_before)
             rho = std::min(0.9, std::max(1e-3, std::pow(eps / eps_before, 1.0 / ran)));
     }
+    for (const auto &L : P32.L)
+        if (L.qstream > 0) {
+            const int f = stream_timeout_flag(s, true);
+            if (f != 0) {
+                loc.cycles = cyc;
+                if (st) *st = loc;
+                return f < 0 ? set_err(ctx, MG_ERR_CUDA, "reading the streaming smoother's flag failed")
+                             : set_err(ctx, MG_ERR_TIMEOUT, "a bounded wait of the streaming smoother gave up");
+            }
+            break;
+        }
     const double c_final = h.c, clamps = h.clamps;
     launch_mean_split<double>(Uu, U64.ncol, &s0->mean, P64.rb, s);
     launch_merge<double>(Uu, n, phi, &s0->mean, s);
@@ -789,6 +829,25 @@ int mg_ctx_set_profiling(mg_ctx *ctx, int on)
 {
     if (!ctx) return MG_ERR_ARG;
     ctx->prof_on = on ? 1 : 0;
+    return MG_OK;
+}
+
+int mg_fp32_smoother_variants(void) { return stream_variants(); }
+
+int mg_ctx_set_fp32_smoother(mg_ctx *ctx, int choice)
+{
+    if (!ctx) return MG_ERR_ARG;
+    if (choice < -1 || choice > stream_variants())
+        return set_err(ctx, MG_ERR_ARG, "fp32 smoother choice %d not in -1 .. %d", choice, stream_variants());
+    ctx->fp32_smoother = choice;
+    // forget the tuning and the graphs that captured it
+    for (auto *m : {&ctx->p32, &ctx->p32c})
+        for (auto &kv : *m) {
+            for (auto &l : kv.second->L) l.qbx = l.qstream = 0;
+            for (auto &g : kv.second->graphs)
+                if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+            kv.second->graphs.clear();
+        }
     return MG_OK;
 }
 
