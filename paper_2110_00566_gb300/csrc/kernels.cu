@@ -93,17 +93,27 @@ k_smooth2(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un
 }
 
 // four cells of an FP32 colour row per thread (rows whose length is a
-// multiple of 4, colour arrays below 2^31 elements)
-template <bool CORR, int MODEL>
-__global__ void __launch_bounds__(256, MODEL == 0 ? 4 : 2) k_smooth4(const float *__restrict__ Uc, const float *__restrict__ Uo, float *__restrict__ Un,
+// multiple of 4, colour arrays below 2^31 elements); a block walks zc
+// consecutive planes (z-marching: the rows of planes i and i+1 it read for
+// plane i are still in L1 when it updates plane i+1)
+template <bool CORR, int MODEL, bool ZM>
+__global__ void __launch_bounds__(256, MODEL == 0 ? (ZM ? 3 : 4) : 2) k_smooth4(const float *__restrict__ Uc, const float *__restrict__ Uo, float *__restrict__ Un,
           const float *__restrict__ Sc, const float *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<float> L,
-          const OpK<float> *__restrict__ opp, int colour, const float *__restrict__ Bc, const float *__restrict__ Bo)
+          const OpK<float> *__restrict__ opp, int colour, const float *__restrict__ Bc, const float *__restrict__ Bo,
+          int zc)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int i = blockIdx.z;
     if (4 * q >= L.half || j >= L.n) return;
-    smooth_quad<CORR, MODEL>(*opp, L, Uc, Uo, Un, Sc, Fc, smooth_cf<float>(sc), colour, Bc, Bo, i, j, 4 * q);
+    if (!ZM) {
+        smooth_quad<CORR, MODEL>(*opp, L, Uc, Uo, Un, Sc, Fc, smooth_cf<float>(sc), colour, Bc, Bo, blockIdx.z, j,
+                                 4 * q);
+        return;
+    }
+    const int i0 = blockIdx.z * zc, i1 = min(L.n, i0 + zc);
+    const float cf = smooth_cf<float>(sc);
+    for (int i = i0; i < i1; ++i)
+        smooth_quad<CORR, MODEL>(*opp, L, Uc, Uo, Un, Sc, Fc, cf, colour, Bc, Bo, i, j, 4 * q);
 }
 
 template <typename T>
@@ -113,16 +123,24 @@ bool launch_smooth4(const LevArrays<T> &, const LevK<T> &, const OpK<T> *, int, 
 }
 
 static bool launch_smooth4_bx(const LevArrays<float> &L, const LevK<float> &K, const OpK<float> *op, int colour,
-                              int nb, int bx, cudaStream_t st)
+                              int nb, int bx, int zc, cudaStream_t st)
 {
     if (L.half % 4 != 0 || L.ncol >= (1LL << 31)) return false;
+    zc = std::max(1, zc);
     const dim3 b = bx > 0 ? dim3(bx, 256 / bx, 1) : block_mj(L.half / 4);
-    const dim3 g = grid_mj(L.half / 4, L.n, b, L.n);
+    const dim3 g = grid_mj(L.half / 4, L.n, b, (L.n + zc - 1) / zc);
     const float *U0 = L.U(colour), *U1 = L.U(1 - colour);
     float *Un = L.u[nb][colour];
 #define MG_SMOOTH4(CORR, MODEL)                                                                              \
-    k_smooth4<CORR, MODEL><<<g, b, 0, st>>>(U0, U1, Un, L.s[colour], L.f[colour], L.sc, K, op, colour,      \
-                                            CORR ? L.base[colour] : nullptr, CORR ? L.base[1 - colour] : nullptr)
+    do {                                                                                                      \
+        const float *b0 = CORR ? L.base[colour] : nullptr, *b1 = CORR ? L.base[1 - colour] : nullptr;        \
+        if (zc > 1)                                                                                           \
+            k_smooth4<CORR, MODEL, true><<<g, b, 0, st>>>(U0, U1, Un, L.s[colour], L.f[colour], L.sc, K, op,  \
+                                                          colour, b0, b1, zc);                                \
+        else                                                                                                  \
+            k_smooth4<CORR, MODEL, false><<<g, b, 0, st>>>(U0, U1, Un, L.s[colour], L.f[colour], L.sc, K, op, \
+                                                           colour, b0, b1, 1);                                \
+    } while (0)
     if (L.base[0]) {
         if (L.model == 0) MG_SMOOTH4(true, 0);
         else if (L.model == 1) MG_SMOOTH4(true, 1);
@@ -141,12 +159,12 @@ bool launch_smooth4<float>(const LevArrays<float> &L, const LevK<float> &K, cons
                            cudaStream_t st)
 {
     if (L.qstream > 0 && launch_smooth_stream(L, K, op, colour, nb, L.qstream, st)) return true;
-    return launch_smooth4_bx(L, K, op, colour, nb, L.qbx, st);
+    return launch_smooth4_bx(L, K, op, colour, nb, L.qbx, L.qz, st);
 }
 
-bool launch_smooth4_shape(const LevArrays<float> &L, const OpK<float> *op, int colour, int bx, cudaStream_t st)
+bool launch_smooth4_shape(const LevArrays<float> &L, const OpK<float> *op, int colour, int bx, int zc, cudaStream_t st)
 {
-    return launch_smooth4_bx(L, make_levk<float>(L.n, L.h), op, colour, 1 - L.cur[colour], bx, st);
+    return launch_smooth4_bx(L, make_levk<float>(L.n, L.h), op, colour, 1 - L.cur[colour], bx, zc, st);
 }
 
 template <typename T>

@@ -25,6 +25,7 @@ struct LevArrays {
     int model = -1;      // operator of the uploaded OpK (0 nDGP, 1 Kmouflage), -1 unknown
     int qbx = 0;         // FP32 four-cell smoother: threads along a row (autotuned; 0 = default)
     int qstream = 0;     // FP32 streaming smoother variant (autotuned; <= 0: the gathering kernel)
+    int qz = 1;          // FP32 four-cell smoother: planes per block (autotuned)
     T *U(int colour) const { return u[cur[colour]][colour]; }
 };
 
@@ -35,10 +36,12 @@ template <typename T>
 void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, int colour, cudaStream_t st);
 template <typename T>
 void launch_smooth_shape(const LevArrays<T> &L, const OpK<T> *op, int colour, int bx, cudaStream_t st);
-// FP32 four-cell half-sweep with bx threads along a row (256 / bx rows) into
-// the alternate buffer, leaving the buffer state untouched (autotuner);
-// false when the level does not use the four-cell kernel
-bool launch_smooth4_shape(const LevArrays<float> &L, const OpK<float> *op, int colour, int bx, cudaStream_t st);
+// FP32 four-cell half-sweep with bx threads along a row (256 / bx rows) and
+// zc planes per block into the alternate buffer, leaving the buffer state
+// untouched (autotuner); false when the level does not use the four-cell
+// kernel
+bool launch_smooth4_shape(const LevArrays<float> &L, const OpK<float> *op, int colour, int bx, int zc,
+                          cudaStream_t st);
 // streaming FP32 four-cell half-sweep (shared-memory plane ring fed by bulk
 // asynchronous copies) for n = 256 and 512: variants 1 .. stream_variants()
 // (ring depth and planes per block); false when the level is not eligible

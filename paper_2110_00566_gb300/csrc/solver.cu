@@ -499,18 +499,24 @@ static void tune_smooth4(mg_ctx *ctx, Pyramid<float> &P)
     cudaStream_t s = ctx->stream;
     for (auto &L : P.L) {
         if (L.qbx != 0 || L.n < 64) continue;
-        int best = 0;
+        int best = 0, best_z = 1;
         float best_ms = 1e30f;
         for (int bx : {8, 16, 32, 64}) {
             if (bx > L.half / 4) continue;
-            if (!launch_smooth4_shape(L, P.opT, 0, bx, s)) break;
-            const float t = time_launch(ctx, [&](int c) { return launch_smooth4_shape(L, P.opT, c, bx, s); });
-            if (t < best_ms) {
-                best_ms = t;
-                best = bx;
+            if (!launch_smooth4_shape(L, P.opT, 0, bx, 1, s)) break;
+            for (int zc : {1, 2, 4, 8}) {
+                if (zc > 1 && L.n < 128) break;
+                const float t =
+                    time_launch(ctx, [&](int c) { return launch_smooth4_shape(L, P.opT, c, bx, zc, s); });
+                if (t < best_ms) {
+                    best_ms = t;
+                    best = bx;
+                    best_z = zc;
+                }
             }
         }
         L.qbx = best > 0 ? best : -1;
+        L.qz = best_z;
         L.qstream = -1;
         if (!stream_eligible(L) || ctx->fp32_smoother < 0) continue;
         if (ctx->fp32_smoother > 0) {
@@ -843,7 +849,10 @@ int mg_ctx_set_fp32_smoother(mg_ctx *ctx, int choice)
     // forget the tuning and the graphs that captured it
     for (auto *m : {&ctx->p32, &ctx->p32c})
         for (auto &kv : *m) {
-            for (auto &l : kv.second->L) l.qbx = l.qstream = 0;
+            for (auto &l : kv.second->L) {
+                l.qbx = l.qstream = 0;
+                l.qz = 1;
+            }
             for (auto &g : kv.second->graphs)
                 if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
             kv.second->graphs.clear();
