@@ -60,6 +60,8 @@ def args():
     p.add_argument("--inner", type=int, default=0, help="FP32 cycles per FP64 defect (0: library default)")
     p.add_argument("--fp32-smoother", type=int, default=0,
                    help="FP32 half-sweep kernel: 0 autotuned, -1 gathering, k >= 1 streaming variant k")
+    p.add_argument("--fp32-shape", default="",
+                   help="pin the gathering FP32 half-sweep shape, n:bx:zc[,n:bx:zc...] (profiling)")
     p.add_argument("--batch", type=int, default=64, help="instances of the batched form (0: skip)")
     p.add_argument("--adj-ng", type=int, default=128, help="mesh of the adjoint form (0: skip)")
     p.add_argument("--pm-adj-ng", type=int, default=128,
@@ -223,6 +225,8 @@ def main():
     ctx = B.Context(local, torch.cuda.current_stream(dev))
     if a.fp32_smoother:
         ctx.set_fp32_smoother(a.fp32_smoother)
+    for item in filter(None, a.fp32_shape.split(",")):
+        ctx.set_fp32_smoother_shape(*(int(x) for x in item.split(":")))
     ng = a.ng
     pos = torch.from_numpy(particles(a, rank)).to(dev)
     delta = torch.empty((ng, ng, ng), dtype=torch.float64, device=dev)
@@ -289,15 +293,18 @@ def main():
         return {"value": upd / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * ng ** 3,
                 "d2h_bytes_per_step": 8 * ng ** 3}
 
-    # DRAM bytes (read + write) per launch of the dominant kernels from ncu at
-    # 256^3 (profiles/k_smooth2_fp64_ndgp_256.md, k_smooth4_fp32corr_ndgp_256.md),
-    # scaled by the cell count to this mesh
-    TRAFFIC_256 = {"fp64": 202.4e6 + 50.3e6, "mixed": 202.4e6 + 24.1e6}
+    # DRAM bytes (read + write) per launch of the dominant kernels from ncu,
+    # with the mesh they were measured on (profiles/k_smooth2_fp64_ndgp_256.md:
+    # FP64 at 256^3; profiles/k_smooth4_fp32corr_ndgp_512.md: the FP32
+    # z-marching half-sweep at 512^3), scaled by the cell count to this mesh
+    TRAFFIC = {"fp64": (202.4e6 + 50.3e6, 256), "mixed": (1673.9e6 + 255.5e6, 512)}
 
     def roofline(r, precision, fp64_tf):
         ms = r["avg_launch_ms"]
-        traffic = TRAFFIC_256[precision] * (ng / 256.0) ** 3
-        tsrc = "ncu dram__bytes_read.sum + dram__bytes_write.sum at 256^3, scaled by (ng/256)^3"
+        tb, tn = TRAFFIC[precision]
+        traffic = tb * (ng / float(tn)) ** 3
+        tsrc = "ncu dram__bytes_read.sum + dram__bytes_write.sum at %d^3%s" % (
+            tn, "" if tn == ng else ", scaled by (ng/%d)^3" % tn)
         if precision == "fp64":
             # finest FP64 half-sweep: read both colours + the colour's s,
             # write the colour = 2 s n^3 bytes (s = 8); FP64-pipe bound

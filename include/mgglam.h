@@ -77,6 +77,15 @@ int mg_ctx_set_profiling(mg_ctx *ctx, int on);
 int mg_ctx_set_fp32_smoother(mg_ctx *ctx, int choice);
 int mg_fp32_smoother_variants(void);
 
+/* Pins the gathering FP32 half-sweep's shape on levels of size n (the
+ * autotuner otherwise picks it on first use): bx threads along a row
+ * (8, 16, 32 or 64, with 4 bx <= n/2; 256 / bx rows per block) and zc
+ * consecutive planes per block (zc >= 1); bx = 0 removes the pin.  For
+ * profiling and reproducible launch configurations; the streaming kernel
+ * is still tried against it under mg_ctx_set_fp32_smoother(0).  Resets the
+ * tuning and the cached cycle graphs.  Errors: MG_ERR_ARG. */
+int mg_ctx_set_fp32_smoother_shape(mg_ctx *ctx, int n, int bx, int zc);
+
 /* Measured FP64 and FP32 fused multiply-add throughput of the context's
  * device in TFLOP/s (an FMA counts 2), from eight independent FMA chains
  * per thread on 16 CTAs per SM: the denominator for kernels bound by plain

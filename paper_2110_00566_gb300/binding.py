@@ -100,6 +100,7 @@ def _declare(L):
         "mg_ctx_workspace_bytes": (C.c_longlong, [_VP]),
         "mg_ctx_set_profiling": (C.c_int, [_VP, C.c_int]),
         "mg_ctx_set_fp32_smoother": (C.c_int, [_VP, C.c_int]),
+        "mg_ctx_set_fp32_smoother_shape": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
         "mg_fp32_smoother_variants": (C.c_int, []),
         "mg_probe_alu_peaks": (C.c_int, [_VP, _P(C.c_double), _P(C.c_double)]),
         "mg_opts_default": (None, [_P(mg_opts)]),
@@ -235,6 +236,10 @@ class Context:
     def set_fp32_smoother(self, choice: int):
         """-1 gathering kernel, 0 autotuned, k >= 1 streaming variant k."""
         return self._rc(lib().mg_ctx_set_fp32_smoother(self.h, int(choice)))
+
+    def set_fp32_smoother_shape(self, n: int, bx: int, zc: int = 1):
+        """Pin the gathering FP32 half-sweep's shape on n^3 levels (bx = 0: unpin)."""
+        return self._rc(lib().mg_ctx_set_fp32_smoother_shape(self.h, int(n), int(bx), int(zc)))
 
     def probe_alu_peaks(self):
         """(FP64, FP32) FMA throughput in TFLOP/s measured on this device."""

@@ -121,6 +121,7 @@ struct mg_ctx {
     // profiling of the finest-level smoother (events recorded in the graphs)
     int prof_on = 0;
     int fp32_smoother = 0;           // -1 gathering kernel, 0 autotuned, k > 0 streaming variant k
+    std::map<int, std::pair<int, int>> fp32_shape;  // pinned (bx, zc) of the gathering kernel per level size
     int prof_k = 0;                  // launches bracketed in the current cycle
     std::vector<cudaEvent_t> pev;    // pairs (start, stop)
 };

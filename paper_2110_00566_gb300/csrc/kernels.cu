@@ -315,8 +315,12 @@ __global__ void __launch_bounds__(256, 2) k_resid_restrict4(const float *__restr
     const double c_old = sc->c;
     const double cshift = c_old - sc->fshift;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    // a block walks a contiguous run of coarse planes, so that the fine
+    // planes shared by consecutive coarse planes are still in L1
+    const int chunk = (nc + gridDim.z - 1) / gridDim.z;
+    const int I0 = blockIdx.z * chunk, I1 = min(nc, I0 + chunk);
     if (4 * K4 < nc && J < nc)
-        for (int I = blockIdx.z; I < nc; I += gridDim.z)
+        for (int I = I0; I < I1; ++I)
             rr_quad<CORR, MODEL>(op, L, U0, U1, S0, S1, F0, F1, B0, B1, cshift, Uc0, Uc1, URc0, URc1, RDc0, RDc1, I,
                                  J, 4 * K4, acc);
     double tot[4];

@@ -501,7 +501,15 @@ static void tune_smooth4(mg_ctx *ctx, Pyramid<float> &P)
         if (L.qbx != 0 || L.n < 64) continue;
         int best = 0, best_z = 1;
         float best_ms = 1e30f;
+        auto pin = ctx->fp32_shape.find(L.n);
+        if (pin != ctx->fp32_shape.end() && launch_smooth4_shape(L, P.opT, 0, pin->second.first, 1, s)) {
+            // pinned shape: still timed, so that a streaming variant must beat it
+            best = pin->second.first;
+            best_z = pin->second.second;
+            best_ms = time_launch(ctx, [&](int c) { return launch_smooth4_shape(L, P.opT, c, best, best_z, s); });
+        }
         for (int bx : {8, 16, 32, 64}) {
+            if (best > 0) break;
             if (bx > L.half / 4) continue;
             if (!launch_smooth4_shape(L, P.opT, 0, bx, 1, s)) break;
             for (int zc : {1, 2, 4, 8}) {
@@ -840,13 +848,9 @@ int mg_ctx_set_profiling(mg_ctx *ctx, int on)
 
 int mg_fp32_smoother_variants(void) { return stream_variants(); }
 
-int mg_ctx_set_fp32_smoother(mg_ctx *ctx, int choice)
+// forget the FP32 smoother tuning and the graphs that captured it
+static void reset_fp32_tuning(mg_ctx *ctx)
 {
-    if (!ctx) return MG_ERR_ARG;
-    if (choice < -1 || choice > stream_variants())
-        return set_err(ctx, MG_ERR_ARG, "fp32 smoother choice %d not in -1 .. %d", choice, stream_variants());
-    ctx->fp32_smoother = choice;
-    // forget the tuning and the graphs that captured it
     for (auto *m : {&ctx->p32, &ctx->p32c})
         for (auto &kv : *m) {
             for (auto &l : kv.second->L) {
@@ -857,6 +861,29 @@ int mg_ctx_set_fp32_smoother(mg_ctx *ctx, int choice)
                 if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
             kv.second->graphs.clear();
         }
+}
+
+int mg_ctx_set_fp32_smoother(mg_ctx *ctx, int choice)
+{
+    if (!ctx) return MG_ERR_ARG;
+    if (choice < -1 || choice > stream_variants())
+        return set_err(ctx, MG_ERR_ARG, "fp32 smoother choice %d not in -1 .. %d", choice, stream_variants());
+    ctx->fp32_smoother = choice;
+    reset_fp32_tuning(ctx);
+    return MG_OK;
+}
+
+int mg_ctx_set_fp32_smoother_shape(mg_ctx *ctx, int n, int bx, int zc)
+{
+    if (!ctx) return MG_ERR_ARG;
+    if (bx == 0) {
+        ctx->fp32_shape.erase(n);
+    } else {
+        if (n < 8 || (bx != 8 && bx != 16 && bx != 32 && bx != 64) || 4 * bx > n / 2 || zc < 1 || zc > n)
+            return set_err(ctx, MG_ERR_ARG, "bad fp32 smoother shape n=%d bx=%d zc=%d", n, bx, zc);
+        ctx->fp32_shape[n] = {bx, zc};
+    }
+    reset_fp32_tuning(ctx);
     return MG_OK;
 }
 

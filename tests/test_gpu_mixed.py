@@ -121,3 +121,32 @@ def test_streaming_smoother_is_bit_identical(B, model, n):
             c.set_fp32_smoother(B.fp32_smoother_variants() + 1)
     finally:
         c.close()
+
+
+def test_pinned_smoother_shapes_are_bit_identical(B):
+    """Pinned block shapes and planes per block of the gathering FP32
+    half-sweep (z-marching on and off) give the same bits as the autotuned
+    choice; bad shapes are rejected."""
+    n, box = 256, 128.0
+    pos, _ = inputs.zeldovich(n // 2, n, box, inputs.pk_cutoff(0.96, 5.0, 0.8), 1.0, seed=13)
+    c = B.Context(0)
+    try:
+        d = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+        B.pm_cic_deposit(c, n, torch.from_numpy(pos).cuda(), d)
+        o = B.opts(rtol=1e-8, precision=B.MG_PREC_MIXED, max_cycles=40)
+        c.set_fp32_smoother(-1)
+        ref = None
+        for bx, zc in [(0, 1), (8, 1), (32, 2), (32, 8), (16, 3)]:
+            c.set_fp32_smoother_shape(n, bx, zc)
+            phi = torch.zeros_like(d)
+            code, _ = B.mg_solve_dgp(c, [dict(ng=n, box_mpch=box, a=1.0, omega_m=0.3, rc_h0=1.0, delta=d, phi=phi)], o)
+            assert code == 0
+            if ref is None:
+                ref = phi
+            else:
+                assert torch.equal(phi, ref), (bx, zc)
+        for bad in [(n, 12, 1), (n, 64, 0), (16, 8, 1)]:
+            with pytest.raises(B.MGError):
+                c.set_fp32_smoother_shape(*bad)
+    finally:
+        c.close()
