@@ -234,7 +234,7 @@ __device__ __forceinline__ void finish_resid(LevScal *sc, const double (&tot)[4]
 // residual norm on one level (both colours); optionally writes -d (old c)
 // as FP32 for the correction solve's source
 // ---------------------------------------------------------------------------
-template <typename T, bool CORR>
+template <typename T, bool CORR, bool ZERO = false>
 __global__ void __launch_bounds__(256)
 k_resid_norm(const T *__restrict__ U0, const T *__restrict__ U1, const T *__restrict__ S0,
              const T *__restrict__ S1, const T *__restrict__ F0, const T *__restrict__ F1, LevScal *sc,
@@ -249,7 +249,8 @@ k_resid_norm(const T *__restrict__ U0, const T *__restrict__ U1, const T *__rest
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     if (m < L.half && j < L.n)
         for (int iz = blockIdx.z; iz < 2 * L.n; iz += gridDim.z)
-            resid_cell<T, CORR>(op, L, U0, U1, S0, S1, F0, F1, B0, B1, D0, D1, cshift, iz & 1, iz >> 1, j, m, acc);
+            resid_cell<T, CORR, -1, ZERO>(op, L, U0, U1, S0, S1, F0, F1, B0, B1, D0, D1, cshift, iz & 1, iz >> 1, j,
+                                          m, acc);
     double tot[4];
     if (grid_sum<4>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0)
         finish_resid(sc, tot, (double)L.n * L.n * L.n, c_old);
@@ -257,14 +258,17 @@ k_resid_norm(const T *__restrict__ U0, const T *__restrict__ U1, const T *__rest
 
 template <typename T>
 void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb, cudaStream_t st,
-                       float *const *D)
+                       float *const *D, bool zero_u)
 {
     const dim3 b = block_mj(L.half);
     dim3 g = grid_mj(L.half, L.n, b, 1);
     g.z = red_z(g, 2 * L.n, rb.cap);
     const LevK<T> K = make_levk<T>(L.n, L.h);
     float *d0 = D ? D[0] : nullptr, *d1 = D ? D[1] : nullptr;
-    if (L.base[0])
+    if (zero_u && !L.base[0])
+        k_resid_norm<T, false, true><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb, K,
+                                                      op, nullptr, nullptr, d0, d1);
+    else if (L.base[0])
         k_resid_norm<T, true><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb, K, op,
                                                L.base[0], L.base[1], d0, d1);
     else
@@ -691,7 +695,7 @@ void launch_set_corr_scalars(LevScal *sc32, const LevScal *sc64, int nlev32, cud
     template void launch_smooth<T>(const LevArrays<T> &, LevArrays<T> *, const OpK<T> *, int, cudaStream_t); \
     template void launch_smooth_shape<T>(const LevArrays<T> &, const OpK<T> *, int, int, cudaStream_t);      \
     template void launch_resid_norm<T>(const LevArrays<T> &, const OpK<T> *, const RedBuf &, cudaStream_t,   \
-                                       float *const *);                                                     \
+                                       float *const *, bool);                                               \
     template void launch_resid_restrict<T>(const LevArrays<T> &, LevArrays<T> &, const OpK<T> *,              \
                                            const RedBuf &, cudaStream_t);                                   \
     template void launch_coarse_source<T>(const LevArrays<T> &, const LevArrays<T> &, const OpK<T> *,         \

@@ -54,10 +54,11 @@ bool launch_smooth_stream(const LevArrays<float> &L, const LevK<float> &K, const
 // last reset, -1 on a CUDA error); synchronises the stream
 int stream_timeout_flag(cudaStream_t st, bool reset);
 // residual norm; with D set also writes -d (with the old c) as FP32,
-// colour-split
+// colour-split; zero_u: the level's u is known to be zero everywhere (the
+// same result from the source alone, without the stencil)
 template <typename T>
 void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb, cudaStream_t st,
-                       float *const *D = nullptr);
+                       float *const *D = nullptr, bool zero_u = false);
 template <typename T>
 void launch_resid_restrict(const LevArrays<T> &Lf, LevArrays<T> &Lc, const OpK<T> *op, const RedBuf &rb,
                            cudaStream_t st);

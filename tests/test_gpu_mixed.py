@@ -150,3 +150,22 @@ def test_pinned_smoother_shapes_are_bit_identical(B):
                 c.set_fp32_smoother_shape(*bad)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cold_start_defect_is_bit_identical(B, ctx, precision):
+    """A solve from phi = 0 evaluates its first defect from the source alone
+    (the stencil of a zero field vanishes); it must give the same bits as a
+    warm start from an explicit zero field, which runs the full stencil."""
+    n = 64
+    delta = 2.0 * inputs.white_noise(n, 14)
+    prec = B.MG_PREC_FP64 if precision == "fp64" else B.MG_PREC_MIXED
+    outs = []
+    for warm in (0, 1):
+        phi = np.zeros_like(delta)
+        code, st = B.mg_solve_dgp(ctx, [dict(ng=n, a=1.0, omega_m=0.3, rc_h0=1.0, delta=delta, phi=phi)],
+                                  B.opts(rtol=1e-9, precision=prec, max_cycles=40, warm_start=warm))
+        assert code == 0
+        outs.append((phi, st[0].eps_list()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
