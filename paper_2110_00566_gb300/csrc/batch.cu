@@ -48,6 +48,7 @@ struct BInst {
     double *s64[2];
     LevScal *sc64;
     LevK<double> K64;    // finest-level constants (h = 1)
+    DgpK64 dk64;         // folded constants of the FP64 nDGP defect (h = 1)
     OpK<float> opf;
     OpK<double> opd;
     double tol;
@@ -182,7 +183,8 @@ __global__ void __launch_bounds__(BTHREADS, 2) k_batch(BatchArgs A)
             if (m < L0.half && j < L0.n)
                 for (int z = zb; z < ze; ++z)
                     resid_cell<double, false, 0>(I.opd, K, I.u64[0], I.u64[1], I.s64[0], I.s64[1], nullptr, nullptr,
-                                                 nullptr, nullptr, L0.f[0], L0.f[1], c_old, z & 1, z >> 1, j, m, acc);
+                                                 nullptr, nullptr, L0.f[0], L0.f[1], c_old, z & 1, z >> 1, j, m, acc,
+                                                 &I.dk64);
             double tot[4];
             const int nt = defect_tiles(L0);
             if (tile_sum<4>(acc, I.partials, I.counter, lt, nt, tot) && threadIdx.x == 0) {
@@ -647,6 +649,7 @@ int solve_batch(mg_ctx *ctx, int count, const mg_instance *inst, const mg_opts &
         B.sc64 = s0;
         B.opf = make_opk<float>(0, alpha, 0, 0.0, 0.0);
         B.opd = make_opk<double>(0, alpha, 0, 0.0, 0.0);
+        B.dk64 = DgpK64{2.0 * (8.0 / 3.0) / 3.0, -1.0 / 6.0};
         B.partials = w->partials + (size_t)q * ctx->batch_partial_cap * 4;
         B.counter = w->counters + 32 * q;
         B.next_active = 1;

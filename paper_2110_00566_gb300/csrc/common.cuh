@@ -70,6 +70,7 @@ struct OpK {
     int model;   // 0 nDGP, 1 Kmouflage
     int nkmo;
     T alpha, abs_alpha, sgn_alpha, alpha2, c83;  // nDGP
+    T a75, sgn75;                                // nDGP: (3/4) alpha, (3/4) sgn(alpha)
     T k1, k2, k3;                                // Kmouflage: 1+gamma b^(n-1), (2n+1)gamma/3, 2(n-1)gamma
 };
 

@@ -54,12 +54,24 @@ OpK<T> make_opk(int model, double alpha, int nkmo, double gamma, double bterm)
     o.sgn_alpha = (T)(alpha >= 0 ? 1.0 : -1.0);
     o.alpha2 = (T)(alpha * alpha);
     o.c83 = (T)(8.0 / 3.0);
+    o.a75 = (T)(0.75 * alpha);
+    o.sgn75 = (T)(alpha >= 0 ? 0.75 : -0.75);
     double bp = 1.0;
     for (int q = 0; q < nkmo - 1; ++q) bp *= bterm;
     o.k1 = (T)(1.0 + gamma * bp);
     o.k2 = (T)((2.0 * nkmo + 1.0) * gamma / 3.0);
     o.k3 = (T)(2.0 * (nkmo - 1) * gamma);
     return o;
+}
+
+// per-level constants of the FP64 nDGP update and residual (the level's
+// spacing only: the operator's own constants stay in device memory, so that
+// captured cycle graphs remain valid when the operator changes)
+template <typename T>
+static DgpK64 dgp_k64(const LevArrays<T> &L)
+{
+    const double h4 = L.h * L.h * L.h * L.h;
+    return DgpK64{2.0 * (8.0 / 3.0) * (1.0 / (3.0 * h4)), -(L.h * L.h) * (1.0 / 6.0)};
 }
 
 // ---------------------------------------------------------------------------
@@ -83,13 +95,13 @@ template <typename T, bool CORR>
 __global__ void __launch_bounds__(256)
 k_smooth2(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un, const T *__restrict__ Sc,
           const T *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<T> L, const OpK<T> *__restrict__ opp,
-          int colour, const T *__restrict__ Bc, const T *__restrict__ Bo)
+          int colour, const T *__restrict__ Bc, const T *__restrict__ Bo, DgpK64 dk)
 {
     const int mp2 = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int i = blockIdx.z;
     if (2 * mp2 >= L.half || j >= L.n) return;
-    smooth_pair<T, CORR>(*opp, L, Uc, Uo, Un, Sc, Fc, smooth_cf<T>(sc), colour, Bc, Bo, i, j, 2 * mp2);
+    smooth_pair<T, CORR>(*opp, L, Uc, Uo, Un, Sc, Fc, smooth_cf<T>(sc), colour, Bc, Bo, i, j, 2 * mp2, dk);
 }
 
 // four cells of an FP32 colour row per thread (rows whose length is a
@@ -179,12 +191,14 @@ void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, in
     if (L.half % 2 == 0) {
         const dim3 b = block_mj(L.half / 2);
         const dim3 g = grid_mj(L.half / 2, L.n, b, L.n);
+        const DgpK64 dk = dgp_k64(L);
         if (L.base[0])
             k_smooth2<T, true><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour],
-                                                L.f[colour], L.sc, K, op, colour, L.base[colour], L.base[1 - colour]);
+                                                L.f[colour], L.sc, K, op, colour, L.base[colour], L.base[1 - colour],
+                                                dk);
         else
             k_smooth2<T, false><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour],
-                                                 L.f[colour], L.sc, K, op, colour, nullptr, nullptr);
+                                                 L.f[colour], L.sc, K, op, colour, nullptr, nullptr, dk);
         Lw->cur[colour] = nb;
         return;
     }
@@ -239,7 +253,7 @@ __global__ void __launch_bounds__(256)
 k_resid_norm(const T *__restrict__ U0, const T *__restrict__ U1, const T *__restrict__ S0,
              const T *__restrict__ S1, const T *__restrict__ F0, const T *__restrict__ F1, LevScal *sc,
              RedBuf rb, LevK<T> L, const OpK<T> *__restrict__ opp, const T *__restrict__ B0,
-             const T *__restrict__ B1, float *__restrict__ D0, float *__restrict__ D1)
+             const T *__restrict__ B1, float *__restrict__ D0, float *__restrict__ D1, DgpK64 dk)
 {
     const OpK<T> op = *opp;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -250,7 +264,7 @@ k_resid_norm(const T *__restrict__ U0, const T *__restrict__ U1, const T *__rest
     if (m < L.half && j < L.n)
         for (int iz = blockIdx.z; iz < 2 * L.n; iz += gridDim.z)
             resid_cell<T, CORR, -1, ZERO>(op, L, U0, U1, S0, S1, F0, F1, B0, B1, D0, D1, cshift, iz & 1, iz >> 1, j,
-                                          m, acc);
+                                          m, acc, &dk);
     double tot[4];
     if (grid_sum<4>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0)
         finish_resid(sc, tot, (double)L.n * L.n * L.n, c_old);
@@ -264,16 +278,17 @@ void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb
     dim3 g = grid_mj(L.half, L.n, b, 1);
     g.z = red_z(g, 2 * L.n, rb.cap);
     const LevK<T> K = make_levk<T>(L.n, L.h);
+    const DgpK64 dk = dgp_k64(L);
     float *d0 = D ? D[0] : nullptr, *d1 = D ? D[1] : nullptr;
     if (zero_u && !L.base[0])
         k_resid_norm<T, false, true><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb, K,
-                                                      op, nullptr, nullptr, d0, d1);
+                                                      op, nullptr, nullptr, d0, d1, dk);
     else if (L.base[0])
         k_resid_norm<T, true><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb, K, op,
-                                               L.base[0], L.base[1], d0, d1);
+                                               L.base[0], L.base[1], d0, d1, dk);
     else
         k_resid_norm<T, false><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb, K, op,
-                                                nullptr, nullptr, d0, d1);
+                                                nullptr, nullptr, d0, d1, dk);
 }
 
 // ---------------------------------------------------------------------------
@@ -285,7 +300,7 @@ k_resid_restrict(const T *__restrict__ U0, const T *__restrict__ U1, const T *__
                  const T *__restrict__ S1, const T *__restrict__ F0, const T *__restrict__ F1, LevScal *sc,
                  RedBuf rb, LevK<T> L, const OpK<T> *__restrict__ opp, T *__restrict__ Uc0, T *__restrict__ Uc1,
                  T *__restrict__ URc0, T *__restrict__ URc1, T *__restrict__ RDc0, T *__restrict__ RDc1,
-                 const T *__restrict__ B0, const T *__restrict__ B1)
+                 const T *__restrict__ B0, const T *__restrict__ B1, DgpK64 dk)
 {
     const OpK<T> op = *opp;
     const int nc = L.n / 2;
@@ -297,7 +312,7 @@ k_resid_restrict(const T *__restrict__ U0, const T *__restrict__ U1, const T *__
     if (K < nc && J < nc)
         for (int I = blockIdx.z; I < nc; I += gridDim.z)
             rr_cell<T, CORR>(op, L, U0, U1, S0, S1, F0, F1, B0, B1, cshift, Uc0, Uc1, URc0, URc1, RDc0, RDc1, I, J, K,
-                             acc);
+                             acc, &dk);
     double tot[4];
     if (grid_sum<4>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0)
         finish_resid(sc, tot, (double)L.n * L.n * L.n, c_old);
@@ -376,14 +391,15 @@ void launch_resid_restrict(const LevArrays<T> &Lf, LevArrays<T> &Lc, const OpK<T
     dim3 g = grid_mj(nc, nc, b, 1);
     g.z = red_z(g, nc, rb.cap);
     const LevK<T> K = make_levk<T>(Lf.n, Lf.h);
+    const DgpK64 dk = dgp_k64(Lf);
     if (Lf.base[0])
         k_resid_restrict<T, true><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb,
                                                    K, op, Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], Lc.fbuf[0],
-                                                   Lc.fbuf[1], Lf.base[0], Lf.base[1]);
+                                                   Lc.fbuf[1], Lf.base[0], Lf.base[1], dk);
     else
         k_resid_restrict<T, false><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc,
                                                     rb, K, op, Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], Lc.fbuf[0],
-                                                    Lc.fbuf[1], nullptr, nullptr);
+                                                    Lc.fbuf[1], nullptr, nullptr, dk);
 }
 
 // ---------------------------------------------------------------------------
