@@ -450,18 +450,6 @@ void launch_coarse_source(const LevArrays<T> &Lf, const LevArrays<T> &Lc, const 
 // ---------------------------------------------------------------------------
 // prolongation + correction (Eq. solution_correction)
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_prolong(T *U0, T *U1, const T *__restrict__ UH0, const T *__restrict__ UH1, const T *__restrict__ RH0,
-          const T *__restrict__ RH1, int n)
-{
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int iz = blockIdx.z;
-    if (m >= n / 2 || j >= n) return;
-    prolong_cell<T>(U0, U1, UH0, UH1, RH0, RH1, n, iz & 1, iz >> 1, j, m);
-}
-
 // four fine cells per thread (FP32, fine rows a multiple of 4 long)
 __global__ void __launch_bounds__(256)
 k_prolong4(float *U0, float *U1, const float *__restrict__ UH0, const float *__restrict__ UH1,
@@ -490,13 +478,46 @@ bool launch_prolong4<float>(const LevArrays<float> &Lf, const LevArrays<float> &
     return true;
 }
 
+// e = u^H - R u^h on the coarse level, in place in the R u buffer: the cycle
+// reads that buffer again only after the next restriction has refilled it
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_coarse_e(const T *__restrict__ UH0, const T *__restrict__ UH1, T *RH0, T *RH1, long long ncol)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncol;
+         q += (long long)gridDim.x * blockDim.x) {
+        RH0[q] = UH0[q] - RH0[q];
+        RH1[q] = UH1[q] - RH1[q];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_prolong_e(T *U0, T *U1, const T *__restrict__ E0, const T *__restrict__ E1, int n)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int iz = blockIdx.z;
+    if (m >= n / 2 || j >= n) return;
+    prolong_cell_e<T>(U0, U1, E0, E1, n, iz & 1, iz >> 1, j, m);
+}
+
+template <typename T>
+int prolong_kernels(const LevArrays<T> &Lf)
+{
+    return (sizeof(T) == 4 && Lf.half % 4 == 0 && Lf.ncol < (1LL << 31)) ? 1 : 2;
+}
+
 template <typename T>
 void launch_prolong(const LevArrays<T> &Lf, const LevArrays<T> &Lc, cudaStream_t st)
 {
     if (launch_prolong4<T>(Lf, Lc, st)) return;
+    const long long nc = Lc.ncol;
+    const int eb = (int)std::min<long long>((nc + 255) / 256, 152LL * 16);
+    k_coarse_e<T><<<eb, 256, 0, st>>>(Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], nc);
     const dim3 b = block_mj(Lf.half);
     const dim3 g = grid_mj(Lf.half, Lf.n, b, 2 * Lf.n);
-    k_prolong<T><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], Lf.n);
+    k_prolong_e<T><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lc.ur[0], Lc.ur[1], Lf.n);
 }
 
 // ---------------------------------------------------------------------------
@@ -717,6 +738,7 @@ void launch_set_corr_scalars(LevScal *sc32, const LevScal *sc64, int nlev32, cud
     template void launch_coarse_source<T>(const LevArrays<T> &, const LevArrays<T> &, const OpK<T> *,         \
                                           const RedBuf &, cudaStream_t);                                    \
     template void launch_prolong<T>(const LevArrays<T> &, const LevArrays<T> &, cudaStream_t);               \
+    template int prolong_kernels<T>(const LevArrays<T> &);                                                  \
     template void launch_coarsest<T>(const LevArrays<T> &, const OpK<double> *, int, cudaStream_t);          \
     template void launch_restrict_plain<T>(T *const[2], int, T *const[2], cudaStream_t);                     \
     template void launch_split<T>(const double *, int, T *const[2], double, const double *, cudaStream_t);   \

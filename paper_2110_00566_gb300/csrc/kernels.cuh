@@ -67,6 +67,9 @@ void launch_coarse_source(const LevArrays<T> &Lf, const LevArrays<T> &Lc, const 
                           cudaStream_t st);
 template <typename T>
 void launch_prolong(const LevArrays<T> &Lf, const LevArrays<T> &Lc, cudaStream_t st);
+// kernels launch_prolong launches for the fine level Lf (1 or 2)
+template <typename T>
+int prolong_kernels(const LevArrays<T> &Lf);
 template <typename T>
 void launch_coarsest(const LevArrays<T> &L, const OpK<double> *op, int sweeps, cudaStream_t st);
 template <typename T>

@@ -275,7 +275,7 @@ template <typename T>
 static long long cycle_launches(const Pyramid<T> &P, const mg_opts &o, int l, int type)
 {
     if (l == P.nlev - 1) return 1;
-    long long c = 2LL * (o.pre + o.post) + 3;
+    long long c = 2LL * (o.pre + o.post) + 2 + prolong_kernels<T>(P.L[l]);
     const int visits = type == MG_CYCLE_W ? 2 : 1;
     for (int v = 0; v < visits; ++v) c += cycle_launches(P, o, l + 1, type);
     if (type == MG_CYCLE_F) c += cycle_launches(P, o, l + 1, MG_CYCLE_V);
