@@ -294,10 +294,10 @@ def main():
                 "d2h_bytes_per_step": 8 * ng ** 3}
 
     # DRAM bytes (read + write) per launch of the dominant kernels from ncu,
-    # with the mesh they were measured on (profiles/k_smooth2_fp64_ndgp_256.md:
-    # FP64 at 256^3; profiles/k_smooth4_fp32corr_ndgp_512.md: the FP32
-    # z-marching half-sweep at 512^3), scaled by the cell count to this mesh
-    TRAFFIC = {"fp64": (202.4e6 + 50.3e6, 256), "mixed": (1673.9e6 + 255.5e6, 512)}
+    # with the mesh they were measured on (profiles/k_smooth2_fp64_ndgp_256.md
+    # and profiles/k_smooth4_fp32corr_ndgp_512.md, both at 512^3), scaled by
+    # the cell count to this mesh
+    TRAFFIC = {"fp64": (1615.6e6 + 518.9e6, 512), "mixed": (1673.9e6 + 255.5e6, 512)}
 
     def roofline(r, precision, fp64_tf):
         ms = r["avg_launch_ms"]
