@@ -96,6 +96,15 @@ __device__ __forceinline__ int mj_tiles(const BLev &L, int planes)
 __device__ __forceinline__ bool quad_level(const BLev &L) { return (L.half & 3) == 0; }
 __device__ __forceinline__ int quad_tiles(const BLev &L) { return cdiv(L.n * L.n * (L.half / 4), BTHREADS); }
 
+// smoother tiles: 256 quads of one plane, walked through SZ consecutive
+// planes on the larger levels (the rows of planes i and i+1 read for plane
+// i are still in L1 for plane i+1)
+__device__ __forceinline__ int smooth_z(const BLev &L) { return L.n >= 128 ? 4 : 1; }
+__device__ __forceinline__ int smooth_tiles(const BLev &L)
+{
+    return cdiv(L.n * (L.half / 4), BTHREADS) * cdiv(L.n, smooth_z(L));
+}
+
 // tiles over the coarse cells (K, J) of plane I of the level below l
 __device__ __forceinline__ int coarse_tiles(const BLev &L)
 {
@@ -265,7 +274,7 @@ __global__ void __launch_bounds__(BTHREADS, 2) k_batch(BatchArgs A)
             const int c = P.colour;
             const int total = prefix([&](int q) {
                 const BLev &L = A.inst[q].lev[d];
-                return d < A.inst[q].nlev - 1 ? (quad_level(L) ? quad_tiles(L) : mj_tiles(L, L.n)) : 0;
+                return d < A.inst[q].nlev - 1 ? (quad_level(L) ? smooth_tiles(L) : mj_tiles(L, L.n)) : 0;
             });
             for (int t = blockIdx.x; t < total; t += gridDim.x) {
                 const int q = find_inst(pref, count, t);
@@ -273,14 +282,17 @@ __global__ void __launch_bounds__(BTHREADS, 2) k_batch(BatchArgs A)
                 const BLev &L = I.lev[d];
                 const LevK<float> &K = L.K;
                 if (quad_level(L)) {
-                    // flat quad index: row (i, j), quad m0 / 4 fastest
-                    const int qr = L.half / 4;
-                    const int Q = (t - pref[q]) * BTHREADS + (int)threadIdx.x;
-                    if (Q < L.n * L.n * qr) {
-                        const int m0 = 4 * (Q % qr), r = Q / qr;
-                        smooth_quad<true, 0>(I.opf, K, L.u[P.cur[c]][c], L.u[P.cur[1 - c]][1 - c],
-                                             L.u[1 - P.cur[c]][c], L.s[c], L.f[c], L.sc->cf32, c, L.base[c],
-                                             L.base[1 - c], r / L.n, r % L.n, m0);
+                    // in-plane quad index (row j, quad m0 / 4 fastest), then the tile's planes
+                    const int qr = L.half / 4, tpp = cdiv(L.n * qr, BTHREADS), Z = smooth_z(L);
+                    const int lt = t - pref[q];
+                    const int Q = (lt % tpp) * BTHREADS + (int)threadIdx.x;
+                    if (Q < L.n * qr) {
+                        const int m0 = 4 * (Q % qr), j = Q / qr;
+                        const int i0 = (lt / tpp) * Z, i1 = min(L.n, i0 + Z);
+                        for (int i = i0; i < i1; ++i)
+                            smooth_quad<true, 0>(I.opf, K, L.u[P.cur[c]][c], L.u[P.cur[1 - c]][1 - c],
+                                                 L.u[1 - P.cur[c]][c], L.s[c], L.f[c], L.sc->cf32, c, L.base[c],
+                                                 L.base[1 - c], i, j, m0);
                     }
                     continue;
                 }
