@@ -450,6 +450,19 @@ void launch_coarse_source(const LevArrays<T> &Lf, const LevArrays<T> &Lc, const 
 // ---------------------------------------------------------------------------
 // prolongation + correction (Eq. solution_correction)
 // ---------------------------------------------------------------------------
+// e = u^H - R u^h on the coarse level, in place in the R u buffer: the cycle
+// reads that buffer again only after the next restriction has refilled it
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_coarse_e(const T *__restrict__ UH0, const T *__restrict__ UH1, T *RH0, T *RH1, long long ncol)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncol;
+         q += (long long)gridDim.x * blockDim.x) {
+        RH0[q] = UH0[q] - RH0[q];
+        RH1[q] = UH1[q] - RH1[q];
+    }
+}
+
 // four fine cells per thread (FP32, fine rows a multiple of 4 long)
 __global__ void __launch_bounds__(256)
 k_prolong4(float *U0, float *U1, const float *__restrict__ UH0, const float *__restrict__ UH1,
@@ -459,7 +472,8 @@ k_prolong4(float *U0, float *U1, const float *__restrict__ UH0, const float *__r
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int iz = blockIdx.z;
     if (4 * q >= n / 2 || j >= n) return;
-    prolong_quad(U0, U1, UH0, UH1, RH0, RH1, n, iz & 1, iz >> 1, j, 4 * q);
+    // the coarse arrays RH hold e = u^H - R u^h (formed by k_coarse_e)
+    prolong_quad<true>(U0, U1, RH0, RH1, nullptr, nullptr, n, iz & 1, iz >> 1, j, 4 * q);
 }
 
 template <typename T>
@@ -474,21 +488,11 @@ bool launch_prolong4<float>(const LevArrays<float> &Lf, const LevArrays<float> &
     if (Lf.half % 4 != 0 || Lf.ncol >= (1LL << 31)) return false;
     const dim3 b = block_mj(Lf.half / 4);
     const dim3 g = grid_mj(Lf.half / 4, Lf.n, b, 2 * Lf.n);
+    const long long nc = Lc.ncol;
+    const int eb = (int)std::min<long long>((nc + 255) / 256, 152LL * 16);
+    k_coarse_e<float><<<eb, 256, 0, st>>>(Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], nc);
     k_prolong4<<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], Lf.n);
     return true;
-}
-
-// e = u^H - R u^h on the coarse level, in place in the R u buffer: the cycle
-// reads that buffer again only after the next restriction has refilled it
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_coarse_e(const T *__restrict__ UH0, const T *__restrict__ UH1, T *RH0, T *RH1, long long ncol)
-{
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncol;
-         q += (long long)gridDim.x * blockDim.x) {
-        RH0[q] = UH0[q] - RH0[q];
-        RH1[q] = UH1[q] - RH1[q];
-    }
 }
 
 template <typename T>
@@ -503,9 +507,9 @@ k_prolong_e(T *U0, T *U1, const T *__restrict__ E0, const T *__restrict__ E1, in
 }
 
 template <typename T>
-int prolong_kernels(const LevArrays<T> &Lf)
+int prolong_kernels(const LevArrays<T> &)
 {
-    return (sizeof(T) == 4 && Lf.half % 4 == 0 && Lf.ncol < (1LL << 31)) ? 1 : 2;
+    return 2;   // the coarse correction, then the prolongation
 }
 
 template <typename T>
