@@ -332,7 +332,9 @@ def main():
         {64, 96, 128, 192, 256}, L = N Mpc/h, N/2 particles per side,
         Zel'dovich at z = 0 with sigma_8 ~ U[0.7, 0.9], H0 r_c log-uniform in
         [0.5, 10] (seed 4 + rank); mixed precision.  The batched call (one
-        persistent kernel) against a loop of single solves."""
+        persistent kernel) against a loop of single mixed-precision solves
+        and against a loop of plain FP64 solves (the FP64 GPU baseline of the
+        forms), with the batched phi's distance to the FP64 loop's."""
         import numpy as np
         from paper_2110_00566_gb300 import inputs
         rng = np.random.default_rng(4 + rank)
@@ -374,10 +376,25 @@ def main():
         ms_s = e0.elapsed_time(e1) / a.steps
         worst = max(float(torch.linalg.vector_norm(x["phi"] - y["phi"]) / torch.linalg.vector_norm(y["phi"]))
                     for x, y in zip(insts, seq))
+        # the plain FP64 loop (one timed pass: it is the slow baseline)
+        o64 = B.opts(rtol=a.rtol, precision=B.MG_PREC_FP64, max_cycles=60)
+        seq64 = [dict(x, phi=torch.zeros_like(x["delta"])) for x in insts]
+        for inst in seq64[:8]:
+            B.mg_solve_dgp(ctx, [dict(inst, phi=torch.zeros_like(inst["delta"]))], o64)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for inst in seq64:
+            B.mg_solve_dgp(ctx, [inst], o64)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms_64 = e0.elapsed_time(e1)
+        worst64 = max(float(torch.linalg.vector_norm(x["phi"] - y["phi"]) / torch.linalg.vector_norm(y["phi"]))
+                      for x, y in zip(insts, seq64))
         cells = sum(x["ng"] ** 3 for x in insts)
         return {"value": upd / a.steps / (ms_b * 1e-3) / 1e9, "unit": UNIT, "instances": a.batch,
                 "total_cells": cells, "ms_per_batch": ms_b, "ms_sequential_loop": ms_s,
                 "speedup_vs_sequential": ms_s / ms_b, "phi_rel_l2_vs_sequential_max": worst,
+                "ms_fp64_loop": ms_64, "speedup_vs_fp64_loop": ms_64 / ms_b, "phi_rel_l2_vs_fp64_max": worst64,
                 "sizes": sorted({x["ng"] for x in insts}), "launch": "one persistent cooperative kernel, graph-captured"}
 
     def adjoint():
