@@ -40,6 +40,7 @@ HBM_PEAK_FALLBACK = 6800.0
 # the two sums of squares (2 x 5), Q (3), Sigma (1), the sqrt argument (2),
 # sqrt (1), N (2), the face sum (2), N + f - c (2), the update (3) = 41
 FLOPS_PER_CELL_FP64 = 41
+FP64_INST_PER_CELL = 36.0   # measured by ncu for the FP64 nDGP half-sweep (FP64-pipe thread instructions per cell)
 
 
 def args():
@@ -316,7 +317,14 @@ def main():
                     "peak_source": "FP64 FMA rate measured by mg_probe_alu_peaks on this GPU",
                     "alg_flops_per_cell": FLOPS_PER_CELL_FP64, "avg_launch_ms": ms, "launches": r["fine_launches"],
                     "hbm_view": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                                 "alg_bytes_per_launch": alg, "peak_source": peak_src}}
+                                 "alg_bytes_per_launch": alg, "peak_source": peak_src},
+                    # the FP64 pipe's view: instructions per updated cell from ncu's
+                    # sm__thread_inst_executed_pipe_fp64 (profiles/k_smooth2_fp64_ndgp_256.md)
+                    # against the probe's FP64 FMA instruction rate (peak / 2 flops)
+                    "fp64_pipe_view": {"instructions_per_cell": FP64_INST_PER_CELL,
+                                       "achieved": FP64_INST_PER_CELL * (ng ** 3 / 2) / (ms * 1e-3) / 1e12,
+                                       "peak": fp64_tf / 2.0, "unit": "T instructions/s",
+                                       "frac": FP64_INST_PER_CELL * (ng ** 3 / 2) / (ms * 1e-3) / 1e12 / (fp64_tf / 2.0)}}
         # finest FP32 correction half-sweep: read e and the base field (both
         # colours, 4 B each), s and f of the colour (2 B each), write the
         # colour (2 B) = 14 n^3 bytes
