@@ -502,6 +502,33 @@ def main():
         out["config"] = "512^3 mesh, L = %g Mpc/h, beta = 0.2, a = 1" % box
         return out
 
+    def cycle_types():
+        """V-, F- and W-cycles on the headline solve (FP64, rtol as the
+        headline): time, cycles and phi's distance to a tight reference
+        (V-cycles to 1e-12), the error-versus-cost comparison of the cycle
+        types."""
+        ref = torch.zeros_like(delta)
+        inst = dict(ng=ng, box_mpch=a.box, a=1.0, omega_m=0.3, rc_h0=a.rc, delta=delta)
+        B.mg_solve_dgp(ctx, [dict(inst, phi=ref)], B.opts(rtol=1e-12, max_cycles=60))
+        out = {}
+        for name, cyc in (("V", B.MG_CYCLE_V), ("F", B.MG_CYCLE_F), ("W", B.MG_CYCLE_W)):
+            o = B.opts(rtol=a.rtol, max_cycles=60, cycle=cyc)
+            phi = torch.zeros_like(delta)
+            B.mg_solve_dgp(ctx, [dict(inst, phi=phi)], o)
+            phi.zero_()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, st = B.mg_solve_dgp(ctx, [dict(inst, phi=phi)], o)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            st = st[0]
+            out[name] = {"ms": e0.elapsed_time(e1), "cycles": st.cycles,
+                         "final_eps_over_eps_ref": st.eps[st.n_eps - 1] / st.eps_ref,
+                         "phi_rel_l2_vs_tight": float(torch.linalg.vector_norm(phi - ref) / torch.linalg.vector_norm(ref))}
+        out["precision"] = "fp64"
+        return out
+
     def adjoint_pm():
         """The differentiable PM run of the adjoint workload: n^3 particles
         on an n^3 mesh, L = 2n Mpc/h, a.pm_adj_steps leapfrog steps from
@@ -563,6 +590,7 @@ def main():
     adj_form = adjoint() if (a.adj_ng > 0 and not a.no_forms) else None
     pm_adj_form = adjoint_pm() if (a.pm_adj_ng > 0 and not a.no_forms) else None
     kmo_form = kmouflage() if not a.no_forms else None
+    cyc_form = cycle_types() if not a.no_forms else None
 
     if rank != 0:
         if dist:
@@ -591,6 +619,8 @@ def main():
         forms["adjoint_pm"] = pm_adj_form
     if kmo_form is not None:
         forms["kmouflage"] = kmo_form
+    if cyc_form is not None:
+        forms["cycle_types"] = cyc_form
     cb = None if a.no_cpu else cpu_baseline(delta.cpu().numpy(), a)
     line = {"metric": METRIC, "value": primary["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": primary["ms_per_step"], "higher_is_better": True,
