@@ -198,13 +198,27 @@ __device__ __forceinline__ void gather2(Nb<T> &v, Nb<T> &w, const T *__restrict_
 // relative error ~ e0^2, about 5e-14, far below the residuals any solve
 // resolves.  Used for x in [0, 1e38] (the clamped nDGP argument; x = 0
 // returns 0).  FP64 runs at 1/63 of the FP32 rate on this GPU and the
-// estimate comes from the FP32 special-function unit.
+// estimate comes from the FP32 special-function unit.  The FP32 image of x
+// and the FP64 images of y0 and y0 / 2 are built with integer operations
+// (IEEE 754 layouts: re-bias the exponent by 1023 - 127 = 896 and move the
+// mantissa; x's mantissa is truncated, which only perturbs the estimate),
+// so that the FP64 pipe — this kernel's bound — issues three instructions
+// for the root; x outside [2^-126, 2^127] takes the clamped conversion.
 __device__ __forceinline__ double k_sqrt(double x)
 {
-    const float xf = fminf(fmaxf((float)x, 1e-30f), 1e38f);
-    const double y = (double)rsqrtf(xf);
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int e = hi >> 20;   // biased exponent (x >= 0)
+    float xf;
+    if (e > 896 && e < 1151)
+        xf = __int_as_float(((hi - (896 << 20)) << 3) | (int)(lo >> 29));
+    else
+        xf = fminf(fmaxf((float)x, 1e-30f), 1e38f);
+    const int yb = __float_as_int(rsqrtf(xf));
+    const double y = __hiloint2double((yb >> 3) + (896 << 20), yb << 29);
+    const double hy = __hiloint2double((yb >> 3) + (895 << 20), yb << 29);   // y / 2
     const double s0 = x * y;
-    return fma(0.5 * y, fma(-s0, s0, x), s0);
+    return fma(hy, fma(-s0, s0, x), s0);
 }
 __device__ __forceinline__ double k_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float k_sqrt(float x)
