@@ -46,25 +46,31 @@ __device__ __forceinline__ void q_terms(const double *__restrict__ u, int n, int
     t[5] = (u[nidx(i, jp, kp, n)] + u[nidx(i, jm, km, n)]) - (u[nidx(i, jp, km, n)] + u[nidx(i, jm, kp, n)]);
 }
 
-// (M^T mu)(i,j,k) = sum_t D_t(kappa_t mu): kappa stored as 6 natural fields
+// (M^T mu)(i,j,k) = sum_t D_t(kappa_t mu).  The three face differences
+// (S_x - S_y, S_x - S_z, S_y - S_z) meet mu at the same six face neighbours,
+// so their kappas are stored combined per face direction:
+//   K[0] = kappa_0 + kappa_1 (x faces), K[1] = kappa_2 - kappa_0 (y faces),
+//   K[2] = -(kappa_1 + kappa_2) (z faces),
+// and K[3..5] = kappa_xy, kappa_xz, kappa_yz (edges, signs by position):
+// 18 fused multiply-adds per cell
 __device__ __forceinline__ double mt_apply(const double *const *__restrict__ K, const double *__restrict__ mu, int n,
                                            int i, int j, int k)
 {
     const int ip = wrap_p(i, n), im = wrap_m(i, n), jp = wrap_p(j, n), jm = wrap_m(j, n);
     const int kp = wrap_p(k, n), km = wrap_m(k, n);
-    auto km_ = [&](int t, int a, int b, int c) {
-        const long long q = nidx(a, b, c, n);
-        return K[t][q] * mu[q];
-    };
     double r = 0.0;
-    // S_x - S_y, S_x - S_z, S_y - S_z: face neighbours with +-1
-    r += km_(0, ip, j, k) + km_(0, im, j, k) - km_(0, i, jp, k) - km_(0, i, jm, k);
-    r += km_(1, ip, j, k) + km_(1, im, j, k) - km_(1, i, j, kp) - km_(1, i, j, km);
-    r += km_(2, i, jp, k) + km_(2, i, jm, k) - km_(2, i, j, kp) - km_(2, i, j, km);
-    // C_ab: edge neighbours
-    r += km_(3, ip, jp, k) + km_(3, im, jm, k) - km_(3, ip, jm, k) - km_(3, im, jp, k);
-    r += km_(4, ip, j, kp) + km_(4, im, j, km) - km_(4, ip, j, km) - km_(4, im, j, kp);
-    r += km_(5, i, jp, kp) + km_(5, i, jm, km) - km_(5, i, jp, km) - km_(5, i, jm, kp);
+    auto add = [&](int t, int a, int b, int c) {
+        const long long q = nidx(a, b, c, n);
+        r = fma(K[t][q], mu[q], r);
+    };
+    auto sub = [&](int t, int a, int b, int c) {
+        const long long q = nidx(a, b, c, n);
+        r = fma(-K[t][q], mu[q], r);
+    };
+    add(0, ip, j, k), add(0, im, j, k), add(1, i, jp, k), add(1, i, jm, k), add(2, i, j, kp), add(2, i, j, km);
+    add(3, ip, jp, k), add(3, im, jm, k), sub(3, ip, jm, k), sub(3, im, jp, k);
+    add(4, ip, j, kp), add(4, im, j, km), sub(4, ip, j, km), sub(4, im, j, kp);
+    add(5, i, jp, kp), add(5, i, jm, km), sub(5, i, jp, km), sub(5, i, jm, kp);
     return r;
 }
 
@@ -100,9 +106,10 @@ k_adj_coef(const double *__restrict__ phi, const double *__restrict__ s, int n, 
         }
         Np[q] = np;
         dNa[q] = dna;
-        K0[q] = 2.0 * qd * t[0] * np;
-        K1[q] = 2.0 * qd * t[1] * np;
-        K2[q] = 2.0 * qd * t[2] * np;
+        // face coefficients combined per direction (see mt_apply)
+        K0[q] = 2.0 * qd * (t[0] + t[1]) * np;
+        K1[q] = 2.0 * qd * (t[2] - t[0]) * np;
+        K2[q] = -2.0 * qd * (t[1] + t[2]) * np;
         K3[q] = 2.0 * qo * t[3] * np;
         K4[q] = 2.0 * qo * t[4] * np;
         K5[q] = 2.0 * qo * t[5] * np;
@@ -121,9 +128,8 @@ __global__ void __launch_bounds__(256) k_adj_v(AdjLev L)
         const int ip = wrap_p(i, n), im = wrap_m(i, n), jp = wrap_p(j, n), jm = wrap_m(j, n);
         const int kp = wrap_p(k, n), km = wrap_m(k, n);
         double r = 0.0;
-        r += K[0][nidx(ip, j, k, n)] + K[0][nidx(im, j, k, n)] - K[0][nidx(i, jp, k, n)] - K[0][nidx(i, jm, k, n)];
-        r += K[1][nidx(ip, j, k, n)] + K[1][nidx(im, j, k, n)] - K[1][nidx(i, j, kp, n)] - K[1][nidx(i, j, km, n)];
-        r += K[2][nidx(i, jp, k, n)] + K[2][nidx(i, jm, k, n)] - K[2][nidx(i, j, kp, n)] - K[2][nidx(i, j, km, n)];
+        r += K[0][nidx(ip, j, k, n)] + K[0][nidx(im, j, k, n)] + K[1][nidx(i, jp, k, n)] + K[1][nidx(i, jm, k, n)];
+        r += K[2][nidx(i, j, kp, n)] + K[2][nidx(i, j, km, n)];
         r += K[3][nidx(ip, jp, k, n)] + K[3][nidx(im, jm, k, n)] - K[3][nidx(ip, jm, k, n)] - K[3][nidx(im, jp, k, n)];
         r += K[4][nidx(ip, j, kp, n)] + K[4][nidx(im, j, km, n)] - K[4][nidx(ip, j, km, n)] - K[4][nidx(im, j, kp, n)];
         r += K[5][nidx(i, jp, kp, n)] + K[5][nidx(i, jm, km, n)] - K[5][nidx(i, jp, km, n)] - K[5][nidx(i, jm, kp, n)];
@@ -152,7 +158,7 @@ k_adj_smooth(AdjLev L, const double *__restrict__ in, double *__restrict__ out, 
                           in[nidx(i, wrap_p(j, n), k, n)] + in[nidx(i, wrap_m(j, n), k, n)] +
                           in[nidx(i, j, wrap_p(k, n), n)] + in[nidx(i, j, wrap_m(k, n), n)];
         const double mt = mt_apply(K, in, n, i, j, k);
-        out[q] = (S6 - h2 * (L.rhs[q] + mt - m * L.v[q])) / 6.0;
+        out[q] = (S6 - h2 * (L.rhs[q] + mt - m * L.v[q])) * (1.0 / 6.0);
     }
 }
 
@@ -165,7 +171,7 @@ k_adj_resid(AdjLev L, const double *__restrict__ lam, const double *__restrict__
     const int n = L.n;
     const long long cnt = (long long)n * n * n;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const double h2 = L.h * L.h;
+    const double inv_h2 = 1.0 / (L.h * L.h);
     const double *K[6] = {L.K[0], L.K[1], L.K[2], L.K[3], L.K[4], L.K[5]};
     const double m = mptr ? *mptr : 0.0;
     double acc[2] = {0.0, 0.0};
@@ -174,7 +180,7 @@ k_adj_resid(AdjLev L, const double *__restrict__ lam, const double *__restrict__
         const double S6 = lam[nidx(wrap_p(i, n), j, k, n)] + lam[nidx(wrap_m(i, n), j, k, n)] +
                           lam[nidx(i, wrap_p(j, n), k, n)] + lam[nidx(i, wrap_m(j, n), k, n)] +
                           lam[nidx(i, j, wrap_p(k, n), n)] + lam[nidx(i, j, wrap_m(k, n), n)];
-        const double Av = (S6 - 6.0 * lam[q]) / h2 - mt_apply(K, lam, n, i, j, k) + m * L.v[q];
+        const double Av = (S6 - 6.0 * lam[q]) * inv_h2 - mt_apply(K, lam, n, i, j, k) + m * L.v[q];
         const double r = L.rhs[q] - Av;
         res[q] = r;
         acc[0] += r * r;
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(256) k_prolong_nat(double *f, int nf, const do
                          9.0 * (c[nidx(I2, J, K, nc)] + c[nidx(I, J2, K, nc)] + c[nidx(I, J, K2, nc)]) +
                          3.0 * (c[nidx(I2, J2, K, nc)] + c[nidx(I2, J, K2, nc)] + c[nidx(I, J2, K2, nc)]) +
                          c[nidx(I2, J2, K2, nc)];
-        f[q] += v / 64.0;
+        f[q] += v * (1.0 / 64.0);
     }
 }
 
