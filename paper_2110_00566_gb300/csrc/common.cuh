@@ -203,17 +203,19 @@ __device__ __forceinline__ void gather2(Nb<T> &v, Nb<T> &w, const T *__restrict_
 // (IEEE 754 layouts: re-bias the exponent by 1023 - 127 = 896 and move the
 // mantissa; x's mantissa is truncated, which only perturbs the estimate),
 // so that the FP64 pipe — this kernel's bound — issues three instructions
-// for the root; x outside [2^-126, 2^127] takes the clamped conversion.
+// for the root; x outside [2^-126, 2^127] takes the seed of the clamped
+// conversion (1e-30 or 1e38).
 __device__ __forceinline__ double k_sqrt(double x)
 {
     const int hi = __double2hiint(x);
     const unsigned lo = (unsigned)__double2loint(x);
     const int e = hi >> 20;   // biased exponent (x >= 0)
-    float xf;
-    if (e > 896 && e < 1151)
-        xf = __int_as_float(((hi - (896 << 20)) << 3) | (int)(lo >> 29));
-    else
-        xf = fminf(fmaxf((float)x, 1e-30f), 1e38f);
+    // outside the float range the seed is the clamped conversion's value,
+    // 1e-30 below (x < 2^-126, zeros included) or 1e38 above, chosen by an
+    // integer select: a double -> float conversion issues on the FP64 pipe,
+    // and a predicated one would be issued for every cell
+    float xf = e <= 896 ? 1e-30f : 1e38f;
+    if (e > 896 && e < 1151) xf = __int_as_float(((hi - (896 << 20)) << 3) | (int)(lo >> 29));
     const int yb = __float_as_int(rsqrtf(xf));
     const double y = __hiloint2double((yb >> 3) + (896 << 20), yb << 29);
     const double hy = __hiloint2double((yb >> 3) + (895 << 20), yb << 29);   // y / 2

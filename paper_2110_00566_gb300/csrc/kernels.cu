@@ -97,11 +97,20 @@ k_smooth2(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un
           const T *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<T> L, const OpK<T> *__restrict__ opp,
           int colour, const T *__restrict__ Bc, const T *__restrict__ Bo, DgpK64 dk)
 {
+    // the smoother's constants, formed once per block (FP64 adds issue at a
+    // small fraction of the integer rate on this GPU)
+    __shared__ T cf_s[2];
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const T cf = smooth_cf<T>(sc);
+        cf_s[0] = cf;
+        cf_s[1] = cf - opp->a75;
+    }
+    __syncthreads();
     const int mp2 = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int i = blockIdx.z;
     if (2 * mp2 >= L.half || j >= L.n) return;
-    smooth_pair<T, CORR>(*opp, L, Uc, Uo, Un, Sc, Fc, smooth_cf<T>(sc), colour, Bc, Bo, i, j, 2 * mp2, dk);
+    smooth_pair<T, CORR>(*opp, L, Uc, Uo, Un, Sc, Fc, cf_s[0], cf_s[1], colour, Bc, Bo, i, j, 2 * mp2, dk);
 }
 
 // four cells of an FP32 colour row per thread (rows whose length is a
@@ -295,7 +304,7 @@ void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb
 // fused residual + FAS restriction, one thread per coarse cell (I, J, K)
 // ---------------------------------------------------------------------------
 template <typename T, bool CORR>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_resid_restrict(const T *__restrict__ U0, const T *__restrict__ U1, const T *__restrict__ S0,
                  const T *__restrict__ S1, const T *__restrict__ F0, const T *__restrict__ F1, LevScal *sc,
                  RedBuf rb, LevK<T> L, const OpK<T> *__restrict__ opp, T *__restrict__ Uc0, T *__restrict__ Uc1,
@@ -410,7 +419,7 @@ template <typename T, bool CORR>
 __global__ void __launch_bounds__(256)
 k_coarse_source(const T *__restrict__ UR0, const T *__restrict__ UR1, const T *__restrict__ S0,
                 const T *__restrict__ S1, T *F0, T *F1, const LevScal *scf, LevScal *scc, RedBuf rb, LevK<T> L,
-                const OpK<T> *__restrict__ opp, const T *__restrict__ B0, const T *__restrict__ B1)
+                const OpK<T> *__restrict__ opp, const T *__restrict__ B0, const T *__restrict__ B1, DgpK64 dk)
 {
     const OpK<T> op = *opp;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -419,7 +428,7 @@ k_coarse_source(const T *__restrict__ UR0, const T *__restrict__ UR1, const T *_
     CsAcc<T> ca;
     if (m < L.half && j < L.n)
         for (int iz = blockIdx.z; iz < 2 * L.n; iz += gridDim.z)
-            cs_cell<T, CORR>(op, L, UR0, UR1, S0, S1, F0, F1, B0, B1, dcf, iz & 1, iz >> 1, j, m, ca);
+            cs_cell<T, CORR>(op, L, UR0, UR1, S0, S1, F0, F1, B0, B1, dcf, iz & 1, iz >> 1, j, m, ca, &dk);
     double acc[2] = {ca.sum(), (double)ca.cl};
     double tot[2];
     if (grid_sum<2>(acc, rb, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
@@ -439,12 +448,13 @@ void launch_coarse_source(const LevArrays<T> &Lf, const LevArrays<T> &Lc, const 
     dim3 g = grid_mj(Lc.half, Lc.n, b, 1);
     g.z = red_z(g, 2 * Lc.n, rb.cap);
     const LevK<T> K = make_levk<T>(Lc.n, Lc.h);
+    const DgpK64 dk = dgp_k64(Lc);
     if (Lc.base[0])
         k_coarse_source<T, true><<<g, b, 0, st>>>(Lc.ur[0], Lc.ur[1], Lc.s[0], Lc.s[1], Lc.fbuf[0], Lc.fbuf[1], Lf.sc,
-                                                  Lc.sc, rb, K, op, Lc.base[0], Lc.base[1]);
+                                                  Lc.sc, rb, K, op, Lc.base[0], Lc.base[1], dk);
     else
         k_coarse_source<T, false><<<g, b, 0, st>>>(Lc.ur[0], Lc.ur[1], Lc.s[0], Lc.s[1], Lc.fbuf[0], Lc.fbuf[1],
-                                                   Lf.sc, Lc.sc, rb, K, op, nullptr, nullptr);
+                                                   Lf.sc, Lc.sc, rb, K, op, nullptr, nullptr, dk);
 }
 
 // ---------------------------------------------------------------------------
