@@ -48,6 +48,28 @@ __device__ __forceinline__ long long fx_in(double x, int ef)
     return (long long)((a ^ neg) - neg);
 }
 
+// the same conversion for an exponent gap emax - E below 32 (a stencil whose
+// exponents span fewer than 32 binades, the usual case away from exact
+// zeros): two 32-bit funnel shifts instead of a general 64-bit shift; the
+// result is identical
+__device__ __forceinline__ long long fx_in_near(double x, int ef)
+{
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned sh = (unsigned)(ef - (hi & 0x7FF00000)) >> 20;            // 0 .. 31
+    const unsigned mh = ((unsigned)hi & 0x000FFFFFu) | 0x00100000u;
+    const unsigned h6 = __funnelshift_l(lo, mh, 6), l6 = lo << 6;           // M 2^6
+    const unsigned long long a = ((unsigned long long)(h6 >> sh) << 32) | __funnelshift_r(l6, h6, sh);
+    const unsigned long long neg = (unsigned long long)(long long)(hi >> 31);
+    return (long long)((a ^ neg) - neg);
+}
+
+template <bool NEAR>
+__device__ __forceinline__ long long fx_cv(double x, int ef)
+{
+    return NEAR ? fx_in_near(x, ef) : fx_in(x, ef);
+}
+
 // a fixed-point integer at the scale of exponent field ef (in place) back to
 // binary64, rounded once to nearest (ties away from zero); |v| < 2^63
 __device__ __forceinline__ double fx_out(long long v, int ef)
@@ -64,20 +86,22 @@ __device__ __forceinline__ double fx_out(long long v, int ef)
     return lz == 64 ? 0.0 : __longlong_as_double((long long)(sgn | (e + m)));
 }
 
-// running maximum of the exponent fields of the 18 stencil neighbours
-__device__ __forceinline__ int fx_emax(const Nb<double> &v, int e)
+// running minimum and maximum of the exponent fields of the 18 stencil
+// neighbours (lo, hi in place)
+__device__ __forceinline__ void fx_range(const Nb<double> &v, int &lo, int &hi)
 {
-    e = max(e, max(fx_ef(v.xp), fx_ef(v.xm)));
-    e = max(e, max(fx_ef(v.yp), fx_ef(v.ym)));
-    e = max(e, max(fx_ef(v.zp), fx_ef(v.zm)));
-    e = max(e, max(fx_ef(v.xpyp), fx_ef(v.xmym)));
-    e = max(e, max(fx_ef(v.xpym), fx_ef(v.xmyp)));
-    e = max(e, max(fx_ef(v.xpzp), fx_ef(v.xmzm)));
-    e = max(e, max(fx_ef(v.xpzm), fx_ef(v.xmzp)));
-    e = max(e, max(fx_ef(v.ypzp), fx_ef(v.ymzm)));
-    e = max(e, max(fx_ef(v.ypzm), fx_ef(v.ymzp)));
-    return e;
+    const int f[18] = {fx_ef(v.xp),   fx_ef(v.xm),   fx_ef(v.yp),   fx_ef(v.ym),   fx_ef(v.zp),   fx_ef(v.zm),
+                       fx_ef(v.xpyp), fx_ef(v.xmym), fx_ef(v.xpym), fx_ef(v.xmyp), fx_ef(v.xpzp), fx_ef(v.xmzm),
+                       fx_ef(v.xpzm), fx_ef(v.xmzp), fx_ef(v.ypzp), fx_ef(v.ymzm), fx_ef(v.ypzm), fx_ef(v.ymzp)};
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        lo = min(lo, f[q]);
+        hi = max(hi, f[q]);
+    }
 }
+
+// the exponents of a stencil (lo, hi from fx_range) take the near conversion
+__device__ __forceinline__ bool fx_near(int lo, int hi) { return hi - lo < (32 << 20); }
 
 // the signed sums of the 19-point stencil, each exact and rounded once:
 // a = Sx - Sy, b = Sx - Sz, amb = a - b = Sz - Sy, the three mixed
@@ -86,18 +110,22 @@ struct FxSums {
     double a, b, amb, cxy, cxz, cyz;
     long long s6;
 };
+template <bool NEAR>
 __device__ __forceinline__ FxSums fx_sums(const Nb<double> &v, int ef)
 {
     FxSums r;
-    const long long X = fx_in(v.xp, ef) + fx_in(v.xm, ef);
-    const long long Y = fx_in(v.yp, ef) + fx_in(v.ym, ef);
-    const long long Z = fx_in(v.zp, ef) + fx_in(v.zm, ef);
+    const long long X = fx_cv<NEAR>(v.xp, ef) + fx_cv<NEAR>(v.xm, ef);
+    const long long Y = fx_cv<NEAR>(v.yp, ef) + fx_cv<NEAR>(v.ym, ef);
+    const long long Z = fx_cv<NEAR>(v.zp, ef) + fx_cv<NEAR>(v.zm, ef);
     r.a = fx_out(X - Y, ef);
     r.b = fx_out(X - Z, ef);
     r.amb = fx_out(Z - Y, ef);
-    r.cxy = fx_out((fx_in(v.xpyp, ef) + fx_in(v.xmym, ef)) - (fx_in(v.xpym, ef) + fx_in(v.xmyp, ef)), ef);
-    r.cxz = fx_out((fx_in(v.xpzp, ef) + fx_in(v.xmzm, ef)) - (fx_in(v.xpzm, ef) + fx_in(v.xmzp, ef)), ef);
-    r.cyz = fx_out((fx_in(v.ypzp, ef) + fx_in(v.ymzm, ef)) - (fx_in(v.ypzm, ef) + fx_in(v.ymzp, ef)), ef);
+    r.cxy = fx_out((fx_cv<NEAR>(v.xpyp, ef) + fx_cv<NEAR>(v.xmym, ef)) -
+                   (fx_cv<NEAR>(v.xpym, ef) + fx_cv<NEAR>(v.xmyp, ef)), ef);
+    r.cxz = fx_out((fx_cv<NEAR>(v.xpzp, ef) + fx_cv<NEAR>(v.xmzm, ef)) -
+                   (fx_cv<NEAR>(v.xpzm, ef) + fx_cv<NEAR>(v.xmzp, ef)), ef);
+    r.cyz = fx_out((fx_cv<NEAR>(v.ypzp, ef) + fx_cv<NEAR>(v.ymzm, ef)) -
+                   (fx_cv<NEAR>(v.ypzm, ef) + fx_cv<NEAR>(v.ymzp, ef)), ef);
     r.s6 = (X + Y) + Z;
     return r;
 }

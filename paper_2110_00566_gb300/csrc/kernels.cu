@@ -92,7 +92,7 @@ k_smooth(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un,
 
 // two cells of a colour row per thread (rows of even length)
 template <typename T, bool CORR>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_smooth2(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un, const T *__restrict__ Sc,
           const T *__restrict__ Fc, const LevScal *__restrict__ sc, LevK<T> L, const OpK<T> *__restrict__ opp,
           int colour, const T *__restrict__ Bc, const T *__restrict__ Bo, DgpK64 dk)
