@@ -19,11 +19,19 @@
 // overflow.  A sum is rounded once on the way back to binary64 (to nearest,
 // ties away from zero), where an FP64 evaluation rounds after every add.
 //
-// Domain.  The fixed-point path needs 60 <= emax <= 2040: every value finite
-// and the largest at least 2^-963 in magnitude.  Zeros and values below
-// 2^(emax - 1081) then shift out to 0, and a converted sum stays in the
-// normal range.  Callers fall back to FP64 arithmetic outside it (a zero
-// field, a NaN or an infinity).
+// The nDGP update also needs the quadratic form of the differences,
+// Q = 16 (a (a - b) + b^2) + 3 (C_xy^2 + C_xz^2 + C_yz^2); with the
+// differences exact integers (|.| < 2^61) Q is formed exactly in 128-bit
+// integer arithmetic (64 x 64 -> 128-bit products, which issue as integer
+// multiply-adds on the otherwise idle FMA pipe): Q >= 0 (both parts are
+// positive semi-definite) and Q < 57 * 2^122 < 2^128, so it is exact as an
+// unsigned 128-bit integer and is rounded once to binary64.
+//
+// Domain.  The fixed-point path needs 570 <= emax <= 1529 (fx_ok): every
+// value finite, the largest between 2^-453 and 2^506 in magnitude.  Zeros and
+// values below 2^(emax - 1081) then shift out to 0, and the converted sums and
+// Q stay in the normal range.  Callers fall back to FP64 arithmetic outside
+// it (a zero field, a NaN or an infinity, extreme magnitudes).
 #pragma once
 #include "common.cuh"
 
@@ -32,8 +40,11 @@ namespace mg {
 // biased exponent field of x, in place (bits 20..30 of the high word)
 __device__ __forceinline__ int fx_ef(double x) { return __double2hiint(x) & 0x7FF00000; }
 
-// the scale's exponent field (in place) admits the fixed-point path
-__device__ __forceinline__ bool fx_ok(int ef) { return ef >= (60 << 20) && ef <= (2040 << 20); }
+// the scale's exponent field (in place) admits the fixed-point path: the
+// quadratic form below (at the squared scale) and every converted sum stay
+// in binary64's normal range for 570 <= emax <= 1529, i.e. the largest value
+// of a stencil between 2^-453 and 2^506 in magnitude
+__device__ __forceinline__ bool fx_ok(int ef) { return ef >= (570 << 20) && ef <= (1529 << 20); }
 
 // x as a fixed-point integer at the scale of exponent field ef (in place)
 __device__ __forceinline__ long long fx_in(double x, int ef)
@@ -103,29 +114,77 @@ __device__ __forceinline__ void fx_range(const Nb<double> &v, int &lo, int &hi)
 // the exponents of a stencil (lo, hi from fx_range) take the near conversion
 __device__ __forceinline__ bool fx_near(int lo, int hi) { return hi - lo < (32 << 20); }
 
-// the signed sums of the 19-point stencil, each exact and rounded once:
-// a = Sx - Sy, b = Sx - Sz, amb = a - b = Sz - Sy, the three mixed
-// differences, and S6 = Sx + Sy + Sz as a fixed-point integer
-struct FxSums {
-    double a, b, amb, cxy, cxz, cyz;
+// unsigned 128-bit integers (two's complement modulo 2^128 for intermediate
+// negative products; every final value here is non-negative)
+struct U128 {
+    unsigned long long lo, hi;
+};
+__device__ __forceinline__ U128 mul_s64(long long a, long long b)
+{
+    U128 r;
+    r.lo = (unsigned long long)a * (unsigned long long)b;
+    r.hi = (unsigned long long)__mul64hi(a, b);
+    return r;
+}
+__device__ __forceinline__ U128 add128(U128 x, U128 y)
+{
+    U128 r;
+    asm("add.cc.u64 %0, %2, %4;\n\taddc.u64 %1, %3, %5;"
+        : "=l"(r.lo), "=l"(r.hi)
+        : "l"(x.lo), "l"(x.hi), "l"(y.lo), "l"(y.hi));
+    return r;
+}
+__device__ __forceinline__ U128 shl128(U128 x, int k)  // 0 < k < 64
+{
+    U128 r;
+    r.hi = (x.hi << k) | (x.lo >> (64 - k));
+    r.lo = x.lo << k;
+    return r;
+}
+
+// Q (an unsigned 128-bit integer at the squared scale of exponent field ef,
+// in place) to binary64, rounded once to nearest (ties away from zero)
+__device__ __forceinline__ double fx_out_q(U128 q, int ef)
+{
+    const bool big = q.hi != 0;
+    const int lzh = __clzll((long long)q.hi), lzl = __clzll((long long)q.lo);
+    const int lz = big ? lzh : 64 + lzl;                  // 128 for Q = 0
+    // the top 64 bits of Q << lz (leading one at bit 63)
+    const unsigned long long top =
+        big ? (lzh == 0 ? q.hi : (q.hi << lzh) | (q.lo >> (64 - lzh))) : (q.lo << (lzl & 63));
+    const unsigned long long m = ((top >> 10) + 1ull) >> 1;
+    // value = Q 2^(2 emax - 2162); leading one at bit 127 - lz of Q, so the
+    // exponent field is (127 - lz) + 2 emax - 1139, added as (field - 1) << 52
+    const unsigned long long e = (unsigned long long)(long long)(2 * (ef >> 20) - 1013 - lz) << 52;
+    return lz == 128 ? 0.0 : __longlong_as_double((long long)(e + m));
+}
+
+// the stencil's signed sums, exact: a = Sx - Sy, b = Sx - Sz, a - b = Sz - Sy,
+// the mixed differences C_xy, C_xz, C_yz and S6 = Sx + Sy + Sz; returns the
+// quadratic form Q of the differences (rounded once) and S6 (as a fixed-point
+// integer), for the nDGP update
+struct FxQuad {
+    double q;
     long long s6;
 };
 template <bool NEAR>
-__device__ __forceinline__ FxSums fx_sums(const Nb<double> &v, int ef)
+__device__ __forceinline__ FxQuad fx_quad(const Nb<double> &v, int ef)
 {
-    FxSums r;
     const long long X = fx_cv<NEAR>(v.xp, ef) + fx_cv<NEAR>(v.xm, ef);
     const long long Y = fx_cv<NEAR>(v.yp, ef) + fx_cv<NEAR>(v.ym, ef);
     const long long Z = fx_cv<NEAR>(v.zp, ef) + fx_cv<NEAR>(v.zm, ef);
-    r.a = fx_out(X - Y, ef);
-    r.b = fx_out(X - Z, ef);
-    r.amb = fx_out(Z - Y, ef);
-    r.cxy = fx_out((fx_cv<NEAR>(v.xpyp, ef) + fx_cv<NEAR>(v.xmym, ef)) -
-                   (fx_cv<NEAR>(v.xpym, ef) + fx_cv<NEAR>(v.xmyp, ef)), ef);
-    r.cxz = fx_out((fx_cv<NEAR>(v.xpzp, ef) + fx_cv<NEAR>(v.xmzm, ef)) -
-                   (fx_cv<NEAR>(v.xpzm, ef) + fx_cv<NEAR>(v.xmzp, ef)), ef);
-    r.cyz = fx_out((fx_cv<NEAR>(v.ypzp, ef) + fx_cv<NEAR>(v.ymzm, ef)) -
-                   (fx_cv<NEAR>(v.ypzm, ef) + fx_cv<NEAR>(v.ymzp, ef)), ef);
+    const long long a = X - Y, b = X - Z, amb = Z - Y;
+    const long long cxy = (fx_cv<NEAR>(v.xpyp, ef) + fx_cv<NEAR>(v.xmym, ef)) -
+                          (fx_cv<NEAR>(v.xpym, ef) + fx_cv<NEAR>(v.xmyp, ef));
+    const long long cxz = (fx_cv<NEAR>(v.xpzp, ef) + fx_cv<NEAR>(v.xmzm, ef)) -
+                          (fx_cv<NEAR>(v.xpzm, ef) + fx_cv<NEAR>(v.xmzp, ef));
+    const long long cyz = (fx_cv<NEAR>(v.ypzp, ef) + fx_cv<NEAR>(v.ymzm, ef)) -
+                          (fx_cv<NEAR>(v.ypzm, ef) + fx_cv<NEAR>(v.ymzp, ef));
+    const U128 E = add128(mul_s64(a, amb), mul_s64(b, b));                                   // E / 2 >= 0
+    const U128 C = add128(add128(mul_s64(cxy, cxy), mul_s64(cxz, cxz)), mul_s64(cyz, cyz));  // >= 0
+    const U128 Q = add128(shl128(E, 4), add128(C, shl128(C, 1)));                             // 16 E/2 + 3 C
+    FxQuad r;
+    r.q = fx_out_q(Q, ef);
     r.s6 = (X + Y) + Z;
     return r;
 }

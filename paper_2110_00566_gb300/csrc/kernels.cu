@@ -71,7 +71,8 @@ template <typename T>
 static DgpK64 dgp_k64(const LevArrays<T> &L)
 {
     const double h4 = L.h * L.h * L.h * L.h;
-    return DgpK64{2.0 * (8.0 / 3.0) * (1.0 / (3.0 * h4)), -(L.h * L.h) * (1.0 / 6.0)};
+    const double k83qd = 2.0 * (8.0 / 3.0) * (1.0 / (3.0 * h4));
+    return DgpK64{k83qd, -(L.h * L.h) * (1.0 / 6.0), k83qd / 16.0};
 }
 
 // ---------------------------------------------------------------------------
