@@ -193,32 +193,27 @@ __device__ __forceinline__ void gather2(Nb<T> &v, Nb<T> &w, const T *__restrict_
 // FP32 result feeds a correction that the FP64 defect of the mixed solve
 // re-measures
 // FP64 square root by one Newton (Heron) step on a single-precision estimate:
-// s0 = x y0 with y0 = rsqrtf(x) (relative error e0 ~ 2^-22), then
-// s1 = s0 + (y0 / 2)(x - s0^2), which approximates s0 + (x - s0^2)/(2 s0);
-// relative error ~ e0^2, about 5e-14, far below the residuals any solve
-// resolves.  Used for x in [0, 1e38] (the clamped nDGP argument; x = 0
-// returns 0).  FP64 runs at 1/63 of the FP32 rate on this GPU and the
-// estimate comes from the FP32 special-function unit.  The FP32 image of x
-// and the FP64 images of y0 and y0 / 2 are built with integer operations
-// (IEEE 754 layouts: re-bias the exponent by 1023 - 127 = 896 and move the
-// mantissa; x's mantissa is truncated, which only perturbs the estimate),
-// so that the FP64 pipe — this kernel's bound — issues three instructions
-// for the root; x outside [2^-126, 2^127] takes the seed of the clamped
-// conversion (1e-30 or 1e38).
+// s0 = x y0 with y0 ~ 1/sqrt(x) (relative error e0 ~ 2^-22 from the FP32
+// special-function unit), then s1 = s0 + (y0 / 2)(x - s0^2), which
+// approximates s0 + (x - s0^2)/(2 s0); relative error ~ e0^2, about 5e-14,
+// far below the residuals any solve resolves.  FP64 runs at 1/63 of the FP32
+// rate on this GPU, so the estimate is formed with integer operations on the
+// IEEE 754 layouts and the FP64 pipe issues three instructions: with
+// x = 1.m 2^(2k + r) (r = 0 or 1), the float 1.m 2^r in [1, 4) (x's mantissa
+// truncated to 23 bits, which only perturbs the estimate) gives
+// rsqrtf = 1.m' 2^q, and y0 = 1.m' 2^(q - k) is that float's bit pattern
+// re-biased to binary64 (exponent + 1023 - 127 - k).  Valid for every
+// positive normal x (and +-0, which return +-0); NaN and infinity give NaN.
 __device__ __forceinline__ double k_sqrt(double x)
 {
     const int hi = __double2hiint(x);
     const unsigned lo = (unsigned)__double2loint(x);
-    const int e = hi >> 20;   // biased exponent (x >= 0)
-    // outside the float range the seed is the clamped conversion's value,
-    // 1e-30 below (x < 2^-126, zeros included) or 1e38 above, chosen by an
-    // integer select: a double -> float conversion issues on the FP64 pipe,
-    // and a predicated one would be issued for every cell
-    float xf = e <= 896 ? 1e-30f : 1e38f;
-    if (e > 896 && e < 1151) xf = __int_as_float(((hi - (896 << 20)) << 3) | (int)(lo >> 29));
+    const int E = ((hi >> 20) & 0x7FF) - 1023;   // unbiased exponent (sign ignored: x >= 0 or -0)
+    const int k = E >> 1, r = E & 1;           // E = 2k + r (floor)
+    const float xf = __int_as_float(((127 + r) << 23) | ((hi & 0x000FFFFF) << 3) | (int)(lo >> 29));
     const int yb = __float_as_int(rsqrtf(xf));
-    const double y = __hiloint2double((yb >> 3) + (896 << 20), yb << 29);
-    const double hy = __hiloint2double((yb >> 3) + (895 << 20), yb << 29);   // y / 2
+    const double y = __hiloint2double((yb >> 3) + ((896 - k) << 20), yb << 29);
+    const double hy = __hiloint2double((yb >> 3) + ((895 - k) << 20), yb << 29);   // y / 2
     const double s0 = x * y;
     return fma(hy, fma(-s0, s0, x), s0);
 }
