@@ -40,7 +40,15 @@ HBM_PEAK_FALLBACK = 6800.0
 # the two sums of squares (2 x 5), Q (3), Sigma (1), the sqrt argument (2),
 # sqrt (1), N (2), the face sum (2), N + f - c (2), the update (3) = 41
 FLOPS_PER_CELL_FP64 = 41
-FP64_INST_PER_CELL = 32.0   # measured by ncu for the FP64 nDGP half-sweep (FP64-pipe thread instructions per cell)
+# Thread instructions per updated cell of the FP64 nDGP half-sweep
+# (k_smooth2<double>, steady state: stencil sums and the quadratic form on
+# the integer pipes), from ncu's sm__inst_executed_pipe_{fp64,alu,fma} and
+# sm__inst_executed counters at 256^3 (profiles/k_smooth2_fp64_ndgp_256.md),
+# and what each pipe issues per SM per clock: ALU and the FMA pipe's integer
+# half 4 sub-partitions x 16 lanes, all instructions 4 x 32; the FP64 rate
+# comes from the probe at run time
+FP64_MIX = {"fp64": 9.0, "alu": 425.0, "fma": 189.5, "issue": 714.0}
+PIPE_RATE = {"alu": 64.0, "fma": 64.0, "issue": 128.0}
 
 
 def args():
@@ -298,7 +306,7 @@ def main():
     # with the mesh they were measured on (profiles/k_smooth2_fp64_ndgp_256.md
     # and profiles/k_smooth4_fp32corr_ndgp_512.md, both at 512^3), scaled by
     # the cell count to this mesh
-    TRAFFIC = {"fp64": (1615.6e6 + 518.9e6, 512), "mixed": (1673.9e6 + 255.5e6, 512)}
+    TRAFFIC = {"fp64": (1616.1e6 + 524.6e6, 512), "mixed": (1673.9e6 + 255.5e6, 512)}
 
     def roofline(r, precision, fp64_tf):
         ms = r["avg_launch_ms"]
@@ -308,23 +316,35 @@ def main():
             tn, "" if tn == ng else ", scaled by (ng/%d)^3" % tn)
         if precision == "fp64":
             # finest FP64 half-sweep: read both colours + the colour's s,
-            # write the colour = 2 s n^3 bytes (s = 8); FP64-pipe bound
+            # write the colour = 2 s n^3 bytes (s = 8).  Bound by its
+            # arithmetic pipes: the peak is the speed of light of its
+            # instruction mix (the busiest pipe's issue time at the sampled SM
+            # clock), and the FP64-only view compares the algorithmic flops
+            # with the FP64 peak an all-FP64 kernel is held to
+            cells = ng ** 3 / 2
             alg = 2 * 8 * ng ** 3
             gbs = alg / (ms * 1e-3) / 1e9
-            tf = FLOPS_PER_CELL_FP64 * (ng ** 3 / 2) / (ms * 1e-3) / 1e12
-            return {"bound": "alu", "achieved": tf, "peak": fp64_tf, "unit": "TFLOP/s", "frac": tf / fp64_tf,
+            tf = FLOPS_PER_CELL_FP64 * cells / (ms * 1e-3) / 1e12
+            mhz = (r.get("clocks") or {}).get("sm_mhz") or 2070.0
+            nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+            rate64 = fp64_tf * 1e12 / 2.0 / (nsm * mhz * 1e6)   # FP64 instructions per clock per SM
+            cyc = {"fp64": FP64_MIX["fp64"] / rate64, "alu": FP64_MIX["alu"] / PIPE_RATE["alu"],
+                   "fma": FP64_MIX["fma"] / PIPE_RATE["fma"], "issue": FP64_MIX["issue"] / PIPE_RATE["issue"]}
+            bind = max(cyc, key=cyc.get)
+            t_sol = cells / nsm * cyc[bind] / (mhz * 1e6)
+            peak = FLOPS_PER_CELL_FP64 * cells / t_sol / 1e12
+            return {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
                     "traffic": traffic, "traffic_source": tsrc, "kernel": "k_smooth2<double> finest half-sweep",
-                    "peak_source": "FP64 FMA rate measured by mg_probe_alu_peaks on this GPU",
+                    "peak_source": "speed of light of the kernel's instruction mix: busiest pipe (%s) at %d "
+                                   "instructions/clock/SM, %.0f MHz, %d SMs" % (
+                                       bind, PIPE_RATE.get(bind, rate64), mhz, nsm),
                     "alg_flops_per_cell": FLOPS_PER_CELL_FP64, "avg_launch_ms": ms, "launches": r["fine_launches"],
+                    "sol_ms_per_launch": t_sol * 1e3, "binding_pipe": bind,
+                    "instructions_per_cell": FP64_MIX, "sm_clocks_per_cell": cyc,
+                    "fp64_only_view": {"achieved": tf, "peak": fp64_tf, "unit": "TFLOP/s", "frac": tf / fp64_tf,
+                                       "peak_source": "FP64 FMA rate measured by mg_probe_alu_peaks on this GPU"},
                     "hbm_view": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                                 "alg_bytes_per_launch": alg, "peak_source": peak_src},
-                    # the FP64 pipe's view: instructions per updated cell from ncu's
-                    # sm__thread_inst_executed_pipe_fp64 (profiles/k_smooth2_fp64_ndgp_256.md)
-                    # against the probe's FP64 FMA instruction rate (peak / 2 flops)
-                    "fp64_pipe_view": {"instructions_per_cell": FP64_INST_PER_CELL,
-                                       "achieved": FP64_INST_PER_CELL * (ng ** 3 / 2) / (ms * 1e-3) / 1e12,
-                                       "peak": fp64_tf / 2.0, "unit": "T instructions/s",
-                                       "frac": FP64_INST_PER_CELL * (ng ** 3 / 2) / (ms * 1e-3) / 1e12 / (fp64_tf / 2.0)}}
+                                 "alg_bytes_per_launch": alg, "peak_source": peak_src}}
         # finest FP32 correction half-sweep: read e and the base field (both
         # colours, 4 B each), s and f of the colour (2 B each), write the
         # colour (2 B) = 14 n^3 bytes
