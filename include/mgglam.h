@@ -455,7 +455,13 @@ int dpm_power_spectrum_adjoint(mg_ctx *ctx, int ng, double box_mpch, int nbins, 
  * For checking each kernel against a reference implementation.  Natural
  * layout FP64 in and out on the context's device (or host); `precision`
  * selects the FP64 (0) or FP32 (1) kernel (inputs are rounded to FP32 on
- * the way in for 1).  The operator is given explicitly:                   */
+ * the way in for 1).  The FP64 nDGP kernels (here and in every FP64 solve)
+ * form the stencil's signed sums and the quadratic form of its differences
+ * exactly in integer arithmetic and round each once to binary64, so their
+ * results are at least as accurate as an all-FP64 evaluation; a stencil
+ * whose largest value lies outside [2^-453, 2^506] in magnitude (a zero
+ * field, NaN, infinity) takes FP64 arithmetic.  The operator is given
+ * explicitly:                                                             */
 typedef struct {
     int model;        /* 0 = nDGP, 1 = Kmouflage                             */
     double alpha;     /* nDGP alpha                                          */
