@@ -459,8 +459,9 @@ int dpm_power_spectrum_adjoint(mg_ctx *ctx, int ng, double box_mpch, int nbins, 
  * form the stencil's signed sums and the quadratic form of its differences
  * exactly in integer arithmetic and round each once to binary64, so their
  * results are at least as accurate as an all-FP64 evaluation; a stencil
- * whose largest value lies outside [2^-453, 2^506] in magnitude (a zero
- * field, NaN, infinity) takes FP64 arithmetic.  The operator is given
+ * whose largest value lies outside [2^-453, 2^506] in magnitude (NaN,
+ * infinity, extreme magnitudes; an all-zero stencil excepted, which is
+ * exact either way) takes FP64 arithmetic.  The operator is given
  * explicitly:                                                             */
 typedef struct {
     int model;        /* 0 = nDGP, 1 = Kmouflage                             */

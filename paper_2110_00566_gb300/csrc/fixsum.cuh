@@ -31,7 +31,8 @@
 // value finite, the largest between 2^-453 and 2^506 in magnitude.  Zeros and
 // values below 2^(emax - 1081) then shift out to 0, and the converted sums and
 // Q stay in the normal range.  Callers fall back to FP64 arithmetic outside
-// it (a zero field, a NaN or an infinity, extreme magnitudes).
+// it (a NaN or an infinity, extreme magnitudes); an all-zero stencil takes
+// the fixed-point path at the scale of 1.0 (fx_zero_scale).
 #pragma once
 #include "common.cuh"
 
@@ -110,6 +111,11 @@ __device__ __forceinline__ void fx_range(const Nb<double> &v, int &lo, int &hi)
         hi = max(hi, f[q]);
     }
 }
+
+// a stencil whose exponent fields are all zero (+-0; subnormals, which this
+// treats as 0) has exact-zero sums at any scale: give it the scale of 1.0, so
+// that it takes the fixed-point path (the first sweep of a solve from phi = 0)
+__device__ __forceinline__ int fx_zero_scale(int hi) { return hi == 0 ? (1023 << 20) : hi; }
 
 // the exponents of a stencil (lo, hi from fx_range) take the near conversion
 __device__ __forceinline__ bool fx_near(int lo, int hi) { return hi - lo < (32 << 20); }
