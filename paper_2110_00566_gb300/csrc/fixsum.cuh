@@ -47,14 +47,18 @@ __device__ __forceinline__ int fx_ef(double x) { return __double2hiint(x) & 0x7F
 // of a stencil between 2^-453 and 2^506 in magnitude
 __device__ __forceinline__ bool fx_ok(int ef) { return ef >= (570 << 20) && ef <= (1529 << 20); }
 
-// x as a fixed-point integer at the scale of exponent field ef (in place)
+// x as a fixed-point integer at the scale of exponent field ef (in place):
+// sign(x) floor(M 2^S / 2^(emax - E)), so x = V 2^(emax - 1075 - S); S = 6
+// for the stencil sums (|V| < 2^59), S = 3 where up to 64 values are summed
+// with integer weights (|V| < 2^56)
+template <int S = 6>
 __device__ __forceinline__ long long fx_in(double x, int ef)
 {
     const int hi = __double2hiint(x);
     const unsigned lo = (unsigned)__double2loint(x);
     const unsigned sh = (unsigned)(ef - (hi & 0x7FF00000)) >> 20;            // emax - E >= 0
     const unsigned mh = ((unsigned)hi & 0x000FFFFFu) | 0x00100000u;          // top 21 bits of M
-    const unsigned long long M6 = ((((unsigned long long)mh) << 32) | lo) << 6;  // M 2^6 < 2^59
+    const unsigned long long M6 = ((((unsigned long long)mh) << 32) | lo) << S;  // M 2^S < 2^(53 + S)
     const unsigned long long a = sh < 64 ? (M6 >> sh) : 0ull;
     const unsigned long long neg = (unsigned long long)(long long)(hi >> 31);  // all ones for x < 0
     return (long long)((a ^ neg) - neg);
@@ -64,26 +68,30 @@ __device__ __forceinline__ long long fx_in(double x, int ef)
 // exponents span fewer than 32 binades, the usual case away from exact
 // zeros): two 32-bit funnel shifts instead of a general 64-bit shift; the
 // result is identical
+template <int S = 6>
 __device__ __forceinline__ long long fx_in_near(double x, int ef)
 {
     const int hi = __double2hiint(x);
     const unsigned lo = (unsigned)__double2loint(x);
     const unsigned sh = (unsigned)(ef - (hi & 0x7FF00000)) >> 20;            // 0 .. 31
     const unsigned mh = ((unsigned)hi & 0x000FFFFFu) | 0x00100000u;
-    const unsigned h6 = __funnelshift_l(lo, mh, 6), l6 = lo << 6;           // M 2^6
+    const unsigned h6 = __funnelshift_l(lo, mh, S), l6 = lo << S;           // M 2^S
     const unsigned long long a = ((unsigned long long)(h6 >> sh) << 32) | __funnelshift_r(l6, h6, sh);
     const unsigned long long neg = (unsigned long long)(long long)(hi >> 31);
     return (long long)((a ^ neg) - neg);
 }
 
-template <bool NEAR>
+template <bool NEAR, int S = 6>
 __device__ __forceinline__ long long fx_cv(double x, int ef)
 {
-    return NEAR ? fx_in_near(x, ef) : fx_in(x, ef);
+    return NEAR ? fx_in_near<S>(x, ef) : fx_in<S>(x, ef);
 }
 
-// a fixed-point integer at the scale of exponent field ef (in place) back to
-// binary64, rounded once to nearest (ties away from zero); |v| < 2^63
+// a fixed-point integer v, worth v 2^(emax - 1075 - S) with ef the exponent
+// field emax in place, back to binary64, rounded once to nearest (ties away
+// from zero); |v| < 2^63.  (S larger than the conversion's folds a power of
+// two into the result: fx_out<S + 6> returns the value divided by 64.)
+template <int S = 6>
 __device__ __forceinline__ double fx_out(long long v, int ef)
 {
     const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
@@ -91,10 +99,10 @@ __device__ __forceinline__ double fx_out(long long v, int ef)
     const int lz = __clzll((long long)a);          // 64 for v = 0
     a <<= (lz & 63);                               // leading one at bit 63
     const unsigned long long m = ((a >> 10) + 1ull) >> 1;  // 53 bits, rounded (2^53 carries into the exponent)
-    // leading one at bit 63 - lz of V, so the value's exponent field is
-    // (63 - lz) + emax - 58; m carries the leading one at bit 52, so the
-    // field is added as (field - 1) << 52
-    const unsigned long long e = (unsigned long long)(long long)((ef >> 20) + 4 - lz) << 52;
+    // leading one at bit 63 - lz of v, so the value's exponent field is
+    // (63 - lz) + emax - 1075 - S + 1023; m carries the leading one at bit
+    // 52, so the field is added as (field - 1) << 52
+    const unsigned long long e = (unsigned long long)(long long)((ef >> 20) + 10 - S - lz) << 52;
     return lz == 64 ? 0.0 : __longlong_as_double((long long)(sgn | (e + m)));
 }
 
