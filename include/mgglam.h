@@ -93,6 +93,26 @@ int mg_ctx_set_fp32_smoother_shape(mg_ctx *ctx, int n, int bx, int zc);
  * paper has no counterpart; this is measurement support.) */
 int mg_probe_alu_peaks(mg_ctx *ctx, double *fp64_tflops, double *fp32_tflops);
 
+/* Accuracy probe of the FP64 arithmetic the FP64 nDGP kernels use in place
+ * of CUDA's IEEE square root and division (those issue many instructions on
+ * this GPU's narrow FP64 pipe): y[q] = f(x[q]) for q < n, with
+ *   fn = 0: the square root (one Heron step on a single-precision
+ *           reciprocal-square-root estimate; relative error below 2^-43 for
+ *           positive normal x),
+ *   fn = 1: the reciprocal 1/x (single-precision estimate and one corrected
+ *           quotient; relative error below 2^-43 for positive normal x below
+ *           2^1022),
+ *   fn = 2: N(Sigma) of Eq. DGP, the Vainshtein term, at Sigma = x[q] for the
+ *           given alpha, N = (3/4)[-alpha + sgn(alpha) sqrt(alpha^2 + 8 Sigma/3)]
+ *           in the rationalised form 2 sgn(alpha) Sigma / (|alpha| + sqrt(...))
+ *           that the kernels evaluate (a cell with Q = 0 and density term
+ *           Sigma; arguments below zero give -(3/4) alpha).
+ * x, y: device arrays of n doubles on the context's device (host pointers
+ * are rejected); alpha: finite and nonzero (read for fn = 2 only).  Queued
+ * on the context's stream.  Errors: MG_ERR_ARG, MG_ERR_CUDA.  (The paper has
+ * no counterpart; this is test support for the kernels' arithmetic.) */
+int mg_probe_fp64_math(mg_ctx *ctx, int fn, const double *x, double *y, long long n, double alpha);
+
 /* ---- problem description (Sec. 3.1.1, 3.2.3, 3.2.4) ------------------- */
 typedef struct {
     int ng;            /* cells per side: 2^k or 3 * 2^k, ng >= 8 (levels halve

@@ -27,7 +27,7 @@
  *     the Kmouflage operator and update.
  *   Sec. 3.1 (GLAM): cloud-in-cell assignment and interpolation.
  *
- * Readings where the paper is silent (all listed in the design doc):
+ * Readings where the paper is silent (the same readings as the GPU path):
  *   - compatibility: on a periodic mesh sum(Lap u) = 0 but the discrete
  *     nonlinear term need not average to zero, so each level's operator is
  *     L(u) = Lap u - N(u) + c with c = <N(u)>, recomputed in every residual

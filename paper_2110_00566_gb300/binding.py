@@ -103,6 +103,7 @@ def _declare(L):
         "mg_ctx_set_fp32_smoother_shape": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
         "mg_fp32_smoother_variants": (C.c_int, []),
         "mg_probe_alu_peaks": (C.c_int, [_VP, _P(C.c_double), _P(C.c_double)]),
+        "mg_probe_fp64_math": (C.c_int, [_VP, C.c_int, _VP, _VP, C.c_longlong, C.c_double]),
         "mg_opts_default": (None, [_P(mg_opts)]),
         "mg_solve_dgp": (C.c_int, [_VP, C.c_int, _P(mg_instance), _P(mg_opts), _P(mg_stats)]),
         "mg_solve_kmouflage": (C.c_int, [_VP, _P(mg_grid), _P(mg_kmo_params), _P(mg_opts), _VP, _VP,
@@ -246,6 +247,13 @@ class Context:
         a, b = C.c_double(), C.c_double()
         self._rc(lib().mg_probe_alu_peaks(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def probe_fp64_math(self, fn: int, x, y, alpha: float = 1.0):
+        """y = f(x) on device float64 tensors with the FP64 kernels' own
+        arithmetic: fn 0 square root, 1 reciprocal, 2 nDGP N(Sigma = x)."""
+        assert x.is_cuda and y.is_cuda and x.dtype == y.dtype and x.numel() == y.numel()
+        self._rc(lib().mg_probe_fp64_math(self.h, int(fn), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                           x.numel(), float(alpha)))
 
     def _rc(self, rc, allow_warn=True):
         if rc < 0 or (rc > 0 and not allow_warn):

@@ -100,9 +100,11 @@ k_adj_coef(const double *__restrict__ phi, const double *__restrict__ s, int n, 
         double np = 0.0, dna = -0.75;
         if (arg > 0.0) {
             const double r = sqrt(arg);
-            np = sg / r;                         // dN/dSigma
-            dna = 0.75 * (-1.0 + sg * alpha / r);  // dN/dalpha at fixed Sigma
-            (void)aa;
+            np = sg / r;  // dN/dSigma
+            // dN/dalpha at fixed Sigma, (3/4)(-1 + sgn(alpha) alpha / r), in
+            // the form that does not cancel for Sigma << alpha^2:
+            // -(3/4)(8 Sigma / 3) / (r (r + |alpha|))
+            dna = -2.0 * sig / (r * (r + aa));
         }
         Np[q] = np;
         dNa[q] = dna;

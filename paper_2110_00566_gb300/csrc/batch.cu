@@ -661,7 +661,7 @@ int solve_batch(mg_ctx *ctx, int count, const mg_instance *inst, const mg_opts &
         B.sc64 = s0;
         B.opf = make_opk<float>(0, alpha, 0, 0.0, 0.0);
         B.opd = make_opk<double>(0, alpha, 0, 0.0, 0.0);
-        B.dk64 = DgpK64{2.0 * (8.0 / 3.0) / 3.0, -1.0 / 6.0, 2.0 * (8.0 / 3.0) / 3.0 / 16.0};
+        B.dk64 = make_dgpk64(1.0);
         B.partials = w->partials + (size_t)q * ctx->batch_partial_cap * 4;
         B.counter = w->counters + 32 * q;
         B.next_active = 1;

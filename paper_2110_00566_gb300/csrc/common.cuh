@@ -217,6 +217,34 @@ __device__ __forceinline__ double k_sqrt(double x)
     const double s0 = x * y;
     return fma(hy, fma(-s0, s0, x), s0);
 }
+// FP64 reciprocal estimate of a positive normal d (below 2^1022) from the
+// single-precision special-function unit: with d = 1.m 2^E, the float 1.m
+// in [1, 2) (d's mantissa truncated to 23 bits) gives rcp = 1.m' 2^q, and the
+// estimate 1.m' 2^(q - E) is that float's bit pattern re-biased to binary64
+// (exponent + 1023 - 127 - E); relative error below 2^-22 (the truncation
+// and the approximate reciprocal, each under 2^-23), no FP64 instruction
+__device__ __forceinline__ double k_rcp_est(double d)
+{
+    const int hi = __double2hiint(d);
+    const unsigned lo = (unsigned)__double2loint(d);
+    const int E = ((hi >> 20) & 0x7FF) - 1023;
+    const float xf = __int_as_float((127 << 23) | ((hi & 0x000FFFFF) << 3) | (int)(lo >> 29));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
+    const int yb = __float_as_int(rf);
+    return __hiloint2double((yb >> 3) + ((896 - E) << 20), yb << 29);
+}
+
+// FP64 quotient a / d for a positive normal d (below 2^1022): q0 = a y with
+// y = k_rcp_est(d) = (1 + e)/d, then one correction by the exact residual
+// a - d q0 (a fused multiply-add): q = q0 + y (a - d q0) = (a/d)(1 - e^2 + ...),
+// relative error about e^2 < 2^-44, three FP64 instructions
+__device__ __forceinline__ double k_quot(double a, double d)
+{
+    const double y = k_rcp_est(d);
+    const double q0 = a * y;
+    return fma(y, fma(-d, q0, a), q0);
+}
 __device__ __forceinline__ double k_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float k_sqrt(float x)
 {
@@ -267,10 +295,10 @@ __device__ __forceinline__ T op_N(const OpK<T> &op, const LevK<T> &L, const Nb<T
             clamp = 1;
             return T(-0.75) * op.alpha;
         }
-        // FP64: the printed form needs no division and its absolute error
-        // (~1e-16 alpha) is far below the residuals the solve resolves; FP32
-        // keeps the rationalised form, which does not cancel for Sigma << alpha^2
-        if (sizeof(T) == 8) return T(0.75) * op.sgn_alpha * (k_sqrt(arg) - op.abs_alpha);
+        // the rationalised form in both precisions: its error is relative to
+        // N itself for any Sigma (the printed difference r - |alpha| cancels
+        // for Sigma << alpha^2, where it would carry the square root's error
+        // relative to alpha)
         return k_div(T(2) * op.sgn_alpha * sig, op.abs_alpha + k_sqrt(arg));
     } else {
         const T dx = v.xp - v.xm, dy = v.yp - v.ym, dz = v.zp - v.zm;

@@ -70,9 +70,7 @@ OpK<T> make_opk(int model, double alpha, int nkmo, double gamma, double bterm)
 template <typename T>
 static DgpK64 dgp_k64(const LevArrays<T> &L)
 {
-    const double h4 = L.h * L.h * L.h * L.h;
-    const double k83qd = 2.0 * (8.0 / 3.0) * (1.0 / (3.0 * h4));
-    return DgpK64{k83qd, -(L.h * L.h) * (1.0 / 6.0), k83qd / 16.0};
+    return make_dgpk64(L.h);
 }
 
 // ---------------------------------------------------------------------------
@@ -102,9 +100,8 @@ k_smooth2(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un
     // small fraction of the integer rate on this GPU)
     __shared__ T cf_s[2];
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-        const T cf = smooth_cf<T>(sc);
-        cf_s[0] = cf;
-        cf_s[1] = cf - opp->a75;
+        cf_s[0] = smooth_cf<T>(sc);
+        cf_s[1] = opp->sgn75 * (T)dk.kq;
     }
     __syncthreads();
     const int mp2 = blockIdx.x * blockDim.x + threadIdx.x;

@@ -544,13 +544,20 @@ extern "C" int pm_cic_deposit_noalloc(int ng, const float *pos, long long np, do
     unsigned int *counter = (unsigned int *)(mean + 1);
     const cudaStream_t st = (cudaStream_t)cuda_stream;
     const long long cnt = (long long)ng * ng * ng;
+    // each launch is checked as it is made, with cudaPeekAtLastError, which
+    // leaves the error state alone: an error left by the caller's earlier
+    // work is neither reported as this call's nor cleared
     k_noalloc_clear<<<grid1(cnt), 256, 0, st>>>(acc, cnt, counter);
+    if (cudaPeekAtLastError() != cudaSuccess) return MG_ERR_CUDA;
     k_cic_deposit<<<grid1(np), 256, 0, st>>>(pos, np, ng, acc);
+    if (cudaPeekAtLastError() != cudaSuccess) return MG_ERR_CUDA;
     k_cic_finish<<<grid1(cnt), 256, 0, st>>>(acc, cnt, (double)cnt / (double)np, delta_out);
+    if (cudaPeekAtLastError() != cudaSuccess) return MG_ERR_CUDA;
     RedBuf rb{partials, counter, NOALLOC_BLOCKS};
     launch_mean_nat(delta_out, cnt, mean, rb, st);
+    if (cudaPeekAtLastError() != cudaSuccess) return MG_ERR_CUDA;
     k_sub_mean<<<grid1(cnt), 256, 0, st>>>(delta_out, cnt, mean);
-    if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) return MG_ERR_CUDA;
     return MG_OK;
 }
 

@@ -1,6 +1,11 @@
 // Throughput probe for the roofline denominators of ALU-bound kernels:
 // FP64 and FP32 fused multiply-add rates of this device, measured with
 // eight independent FMA chains per thread on a grid of 16 CTAs per SM.
+// Accuracy probe of the FP64 square root, quotient and nDGP N(Sigma) that
+// the FP64 kernels evaluate, for tests against CUDA's IEEE operations.
+#include <algorithm>
+
+#include "cells.cuh"
 #include "ctx.cuh"
 
 namespace mg {
@@ -40,7 +45,50 @@ static double probe_one(mg_ctx *ctx, int iters)
     return 2.0 * fmas / (ms * 1e-3) / 1e12;
 }
 
+// y[q] = f(x[q]) with the kernels' own device functions
+__global__ void __launch_bounds__(256)
+k_math_probe(const double *__restrict__ x, double *__restrict__ y, long long n, int fn, OpK<double> op, DgpK64 dk)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += stride) {
+        const double v = x[q];
+        double r;
+        if (fn == 0) {
+            r = k_sqrt(v);
+        } else if (fn == 1) {
+            r = k_quot(1.0, v);
+        } else {
+            // a cell whose stencil has Q = 0 and density term s = v on a level
+            // of spacing h = 1: the residual kernels' N
+            int cl = 0;
+            r = dgp64_N(op, dk, fma(dk.w24, v, 0.0), cl);
+        }
+        y[q] = r;
+    }
+}
+
 }  // namespace mg
+
+extern "C" int mg_probe_fp64_math(mg_ctx *ctx, int fn, const double *x, double *y, long long n, double alpha)
+{
+    if (!ctx || !x || !y || n < 0 || fn < 0 || fn > 2) return MG_ERR_ARG;
+    if (n == 0) return MG_OK;
+    if (!mg::is_device_ptr(x) || !mg::is_device_ptr(y))
+        return mg::set_err(ctx, MG_ERR_ARG, "mg_probe_fp64_math: x and y must be device pointers");
+    if (fn == 2 && !(alpha != 0.0 && alpha == alpha && alpha - alpha == 0.0))
+        return mg::set_err(ctx, MG_ERR_ARG, "mg_probe_fp64_math: alpha must be finite and nonzero");
+    try {
+        mg::enter(ctx);
+        mg::OpK<double> op = mg::make_opk<double>(0, alpha, 2, 0.0, 0.0);
+        const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
+        mg::k_math_probe<<<(unsigned)blocks, 256, 0, ctx->stream>>>(x, y, n, fn, op, mg::make_dgpk64(1.0));
+        MG_CK(cudaGetLastError());
+        mg::leave(ctx);
+    } catch (mg::CudaFail &f) {
+        return f.code;
+    }
+    return MG_OK;
+}
 
 extern "C" int mg_probe_alu_peaks(mg_ctx *ctx, double *fp64_tflops, double *fp32_tflops)
 {

@@ -69,3 +69,36 @@ def test_batch_repeated_calls_are_deterministic(B, ctx):
         outs.append([p.cpu().numpy() for p in phis])
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
+
+
+def test_batch_at_the_benchmarked_sizes(B, ctx):
+    """One batched call over instances of every size of the benchmarked
+    ensemble (64, 96, 128, 192 and 256 cells per side; L = N Mpc/h): the
+    persistent kernel's four-cell and z-marching tiles (levels of 128^3 and
+    more) and the 6^3-coarsest hierarchies of the 3 * 2^k sizes.  Each
+    instance must satisfy the oracle's own discrete system at the requested
+    relative residual (eps/eps_ref <= 1.01e-8 for the oracle's operator on
+    the GPU's phi, a property that holds at any size), and the 64^3
+    instance must match the oracle's solution element by element (1e-6
+    relative L2)."""
+    sizes = [64, 96, 128, 192, 256, 64]
+    probs = _instances(sizes, 9)
+    dev = torch.device("cuda", 0)
+    insts, phis = [], []
+    for n, rc, delta in probs:
+        d = torch.from_numpy(delta).to(dev)
+        p = torch.zeros_like(d)
+        phis.append(p)
+        insts.append(dict(ng=n, box_mpch=float(n), a=1.0, omega_m=0.3, rc_h0=rc, delta=d, phi=p))
+    code, stats = B.mg_solve_dgp(ctx, insts, B.opts(rtol=1e-8, precision=B.MG_PREC_MIXED, max_cycles=60))
+    assert code == 0, [s.eps_list() for s in stats]
+    for q, ((n, rc, delta), p, st) in enumerate(zip(probs, phis, stats)):
+        s0, eps_ref, alpha, _ = oracle.dgp_source(delta, 1.0, 0.3, rc)
+        assert abs(st.eps_ref - eps_ref) < 1e-10 * eps_ref
+        got = p.cpu().numpy()
+        _, _, eps = oracle.residual(oracle.dgp_op(alpha), got, s0, None, 1.0)
+        assert eps <= 1.01e-8 * eps_ref, (n, rc, eps / eps_ref)
+        assert abs(got.mean()) < 1e-12 * np.abs(got).max()
+        if q == 0:
+            ref, _ = oracle.dgp_solve(delta, 1.0, 0.3, rc, oracle.Opts(rtol=1e-11, max_cycles=60))
+            assert np.linalg.norm(got - ref) < 1e-6 * np.linalg.norm(ref), (n, rc)

@@ -40,3 +40,40 @@ def test_512_solutions_satisfy_the_discrete_system(B, ctx):
         del u
     p64, pmx = sols[B.MG_PREC_FP64], sols[B.MG_PREC_MIXED]
     assert np.linalg.norm(pmx - p64) < 1e-6 * np.linalg.norm(p64)
+
+
+@pytest.mark.parametrize("nk,k0", [(2, 1.0), (3, 1.0)])
+def test_512_kmouflage_solutions_satisfy_the_discrete_system(B, ctx, nk, k0):
+    """The Kmouflage workload at full size (Sec. 3.2.4, Eq.
+    kmf_eqn_codeunit_final over c~): a 512^3 mesh in a 512 Mpc/h box, the
+    Zel'dovich load of 256^3 particles at z = 0 (seed 3), beta = 0.2, a = 1,
+    lambda, phibar'/H0 and A(phibar) from the oracle's background solve of
+    the model.  The FP64 and the mixed-precision GPU solves must satisfy
+    the oracle's discrete system to eps/eps_ref <= 1.01e-8, and agree to
+    1e-6 relative L2 (the error of the mixed form against the FP64
+    solution of the same system)."""
+    from oracle import background as ob
+    ng, nps, box, a, om, beta = 512, 256, 512.0, 1.0, 0.3, 0.2
+    pos, _ = inputs.zeldovich(nps, ng, box, inputs.pk_cutoff(0.96, 5.0, 0.8), 1.0, seed=3)
+    delta, _ = oracle.cic_deposit(pos, ng, nps)
+    lam, tab = ob.solve(ob.Background(n=nk, k0=k0, beta=beta), np.array([1.0]))
+    dphi_h0, A_bar = float(tab[0, 4]), float(tab[0, 3])
+    s0, eps_ref = oracle.kmo_source(delta, a, om, ng, box, beta, A_bar)
+    op = oracle.kmo_op(nk, oracle.gamma_kmo(nk, k0, a, lam), dphi_h0 ** 2)
+    d = torch.from_numpy(delta).cuda()
+    del delta
+    sols = {}
+    for prec in (B.MG_PREC_FP64, B.MG_PREC_MIXED):
+        phi = torch.zeros_like(d)
+        code, st = B.mg_solve_kmouflage(ctx, ng, box, a, om, nk, k0, beta, lam, dphi_h0, A_bar, d, phi,
+                                        B.opts(rtol=1e-8, precision=prec, max_cycles=60))
+        assert code == 0
+        assert abs(st.eps_ref - eps_ref) < 1e-10 * eps_ref
+        u = phi.cpu().numpy()
+        sols[prec] = u
+        _, c, eps = oracle.residual(op, u, s0, None, 1.0)
+        assert eps <= 1.01e-8 * eps_ref, (prec, eps / eps_ref)
+        assert abs(u.mean()) < 1e-12 * np.abs(u).max()
+        del u
+    p64, pmx = sols[B.MG_PREC_FP64], sols[B.MG_PREC_MIXED]
+    assert np.linalg.norm(pmx - p64) < 1e-6 * np.linalg.norm(p64)

@@ -2,16 +2,19 @@
 cannot let a library allocate device memory (graph capture, caller-owned
 memory pools, pipelines that cannot take cudaMalloc's synchronisation).
 
-Called through the C-ABI on device arrays, twice in a row with different
-particle loads (the shared static scratch keeps the previous call's
-contents, so the second result also checks that every call clears it), and
-compared with the allocating entry point pm_cic_deposit.  Collected last,
-so that a run that stops at the first failure has run everything else."""
+Called through the C-ABI on device arrays, several times in a row with
+different particle loads and mesh sizes up to the scratch array's limit of
+128^3 cells (the shared static scratch keeps the previous call's contents,
+so each later result also checks that every call clears it), and compared
+with the allocating entry point pm_cic_deposit (1e-12) and with the oracle's
+FP64 CIC density (within the fixed-point sums' bound).  Collected last, so
+that a run that stops at the first failure has run everything else."""
 import ctypes as C
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2110_00566_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -34,7 +37,7 @@ def test_noalloc_deposit_matches_allocating_deposit(lib):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     try:
-        for seed, ng, nps in ((11, 64, 32), (12, 96, 48)):
+        for seed, ng, nps in ((11, 64, 32), (12, 96, 48), (13, 128, 64), (14, 128, 128), (15, 32, 16)):
             pos_h, _ = inputs.zeldovich(nps, ng, 2.0 * ng, inputs.pk_cutoff(), 1.0, seed=seed)
             pos = torch.from_numpy(pos_h).to(dev)
             ref = torch.empty((ng,) * 3, dtype=torch.float64, device=dev)
@@ -47,6 +50,12 @@ def test_noalloc_deposit_matches_allocating_deposit(lib):
             diff = (out - ref).abs().max().item()
             assert diff <= 1e-12, diff
             assert abs(out.mean().item()) < 1e-12
+            # against the oracle: each CIC weight is summed as a 32.32
+            # fixed-point number (at most 2^-33 from the FP64 weight), the
+            # bound of the allocating deposit's own parity test
+            orc, _ = oracle.cic_deposit(pos_h, ng, nps)
+            scale = float(ng) ** 3 / pos_h.shape[0]
+            assert np.abs(out.cpu().numpy() - orc).max() < 1e-8 * scale
     finally:
         ctx.close()
 
