@@ -2,18 +2,21 @@
 """Benchmark of the hot path: the nDGP (Vainshtein) multigrid field solve of
 MG-GLAM (arXiv:2110.00566, Sec. 3.2) on a 512^3 periodic mesh.
 
-Workload (synthetic, seeded): 256^3 particles in a 256 Mpc/h box, displaced
-from a lattice by the Zel'dovich field of P(k) = A k^0.96 exp(-k/5) with
-sigma_8 = 0.8 evaluated at z = 0 (seed 2 + rank), deposited by CIC on the
-512^3 mesh; a = 1, Omega_m = 0.3, H0 r_c = 1.  One step = one complete
-solve from phi = 0 to eps/eps_ref < 1e-8 with V(2,2) cycles (source prep,
-all cycles, gauge fix), inputs resident in HBM.  The metric is smoother
-cell-updates (summed over all levels and cycles) per second.
+Workload (synthetic, seeded): the particle-mesh run of Sec. 3.1 that the
+solve sits in -- 256^3 particles in a 256 Mpc/h box from Zel'dovich initial
+conditions at z = 100 (P(k) = A k^0.96 exp(-k/5), sigma_8 = 0.8, seed 2 +
+rank), 100 leapfrog steps of constant da to z = 0 on the 512^3 mesh with an
+FP64 nDGP solve (H0 r_c = 1, warm-started) at every step -- and, as the
+timed step, the nDGP solve of that run's z = 0 CIC density: a = 1,
+Omega_m = 0.3, from phi = 0 to eps/eps_ref < 1e-8 with V(2,2) cycles
+(source prep, all cycles, gauge fix), inputs resident in HBM.  The metric
+is smoother cell-updates (summed over all levels and cycles) per second.
 
 `value` is the FP64 solve (every level FP64, the paper's precision).  The
-same line reports the mixed-precision form (FP32 correction cycles, FP64
-defect) under "forms", timed the same way, with its speedup and its phi
-difference from the FP64 solution.
+same line reports the forms under "forms" (mixed precision, the batched
+ensemble, the adjoint, the 100-step run itself at H0 r_c = 1 and 5, the
+Kmouflage solves, the cycle types) and a compact "forms_summary" as its
+last key.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
   python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
@@ -77,6 +80,11 @@ def args():
                    help="mesh (= particles per side) of the differentiable PM run (0: skip)")
     p.add_argument("--pm-adj-steps", type=int, default=20)
     p.add_argument("--fd-dirs", type=int, default=16, help="finite-difference directions for the PM gradient")
+    p.add_argument("--pm-steps", type=int, default=100,
+                   help="leapfrog steps of the particle-mesh run whose z = 0 density is the solve's input "
+                        "(0: the Zel'dovich field at z = 0 instead)")
+    p.add_argument("--cpu-full-ng", type=int, default=256,
+                   help="mesh of the oracle's complete solve in the CPU baseline (0: skip)")
     return p.parse_args()
 
 
@@ -155,10 +163,70 @@ def cpu_baseline(delta_host, a, sample_cycles=1):
         cells = (ng >> l) ** 3
         per_cycle += (oracle.Opts().coarse_sweeps if l == levels - 1 else 4) * cells
     updates = per_cycle * st.cycles
-    return {"value": updates / dt / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d V(2,2) cycle(s) of the %d^3 solve (with its initial and final residual passes), "
-                      "plain C FP64 oracle, OpenMP over i-planes" % (st.cycles, ng),
-            "seconds": dt}
+    out = {"value": updates / dt / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "%d V(2,2) cycle(s) of the %d^3 solve (with its initial and final residual passes), "
+                     "plain C FP64 oracle, OpenMP over i-planes" % (st.cycles, ng),
+           "seconds": dt}
+    if getattr(a, "cpu_full_ng", 0) > 0:
+        out["full_solve"] = cpu_full_solve(a.cpu_full_ng, a)
+    return out
+
+
+def cpu_full_solve(n, a):
+    """The oracle's complete solve to eps/eps_ref < rtol on a smaller mesh of
+    the same resolution (n^3 cells, (n/2)^3 Zel'dovich particles at z = 0,
+    L = n/2 Mpc/h, seed 2): the CPU time of a whole solve, not a sample."""
+    import oracle
+    from paper_2110_00566_gb300 import inputs
+    pos, _ = inputs.zeldovich(n // 2, n, n / 2.0, inputs.pk_cutoff(0.96, 5.0, 0.8), 1.0, seed=2)
+    delta, _ = oracle.cic_deposit(pos, n, n // 2)
+    t = time.perf_counter()
+    u, st = oracle.dgp_solve(delta, 1.0, 0.3, a.rc, oracle.Opts(rtol=a.rtol, max_cycles=60))
+    dt = time.perf_counter() - t
+    levels = oracle.num_levels(n)
+    per_cycle = sum((oracle.Opts().coarse_sweeps if l == levels - 1 else 4) * (n >> l) ** 3 for l in range(levels))
+    return {"value": per_cycle * st.cycles / dt / 1e9, "unit": UNIT, "ms_per_solve": dt * 1e3,
+            "cycles": st.cycles, "cores": os.cpu_count(),
+            "sample": "complete FP64 solve to eps/eps_ref < %g of a %d^3 mesh (CIC of %d^3 Zel'dovich particles "
+                      "at z = 0, L = %g Mpc/h), plain C oracle, OpenMP over i-planes" % (a.rtol, n, n // 2, n / 2.0)}
+
+
+def summarise(line, primary):
+    """A compact digest of the forms, the line's last key: each form as a
+    speedup over the plain FP64 GPU solve (the headline), with the numbers
+    it rests on."""
+    f = line.get("forms", {})
+
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return round(d, 4) if isinstance(d, float) else d
+
+    out = {"fp64_ms": round(primary["ms_per_step"], 2), "fp64_hbm_frac": g(line, "roofline", "frac"),
+           "mixed_ms": g(f, "mixed", "ms_per_step"), "mixed_speedup_at_rtol": g(f, "mixed", "speedup_vs_primary"),
+           "mixed_hbm_frac": g(f, "mixed", "roofline", "frac"),
+           "at_1e-6_fp64_ms": g(f, "at_equal_accuracy", "fp64", "ms"),
+           "at_1e-6_mixed_ms": g(f, "at_equal_accuracy", "mixed", "ms"),
+           "at_1e-6_mixed_speedup": g(f, "at_equal_accuracy", "mixed_speedup"),
+           "batched_ms": g(f, "batched", "ms_per_batch"),
+           "batched_speedup_vs_fp64_loop": g(f, "batched", "speedup_vs_fp64_loop"),
+           "batched_speedup_vs_mixed_loop": g(f, "batched", "speedup_vs_sequential"),
+           "batched_at_1e-6_speedup_vs_fp64_loop": g(f, "batched", "at_equal_accuracy", "speedup_vs_fp64_loop"),
+           "adjoint_backward_over_forward": g(f, "adjoint", "backward_over_forward"),
+           "adjoint_pm_reverse_over_forward": g(f, "adjoint_pm", "reverse_over_forward"),
+           "pm100_rc1_ms_per_step": g(f, "pm_run", "rc1", "ms_per_step"),
+           "pm100_rc1_solve_share": g(f, "pm_run", "rc1", "solve_share"),
+           "pm100_rc1_cycles_per_step": g(f, "pm_run", "rc1", "cycles_per_step_mean"),
+           "pm100_rc5_ms_per_step": g(f, "pm_run", "rc5", "ms_per_step"),
+           "rc5_fp64_ms": g(f, "rc5", "fp64", "ms_per_solve"), "rc5_mixed_ms": g(f, "rc5", "mixed", "ms_per_solve"),
+           "kmo_n2_fp64_ms": g(f, "kmouflage", "n2_K0_1", "fp64", "ms"),
+           "kmo_n2_mixed_ms": g(f, "kmouflage", "n2_K0_1", "mixed", "ms"),
+           "kmo_n3_fp64_ms": g(f, "kmouflage", "n3_K0_1", "fp64", "ms"),
+           "kmo_n3_mixed_ms": g(f, "kmouflage", "n3_K0_1", "mixed", "ms"),
+           "cpu_full_solve_ms": g(line, "cpu_baseline", "full_solve", "ms_per_solve")}
+    return {k: v for k, v in out.items() if v is not None}
 
 
 def reduce_over_ranks(dist, ms, updates, device):
@@ -175,14 +243,19 @@ def reduce_over_ranks(dist, ms, updates, device):
 
 
 def workload_name(a):
-    return ("nDGP FAS V(2,2) solve to eps/eps_ref<%g, %d^3 mesh, CIC of %d^3 Zel'dovich particles "
-            "(P~k^0.96 e^-k/5, sigma8=0.8, z=0), L=%g Mpc/h, a=1, Omega_m=0.3, H0 rc=%g"
-            % (a.rtol, a.ng, a.np, a.box, a.rc))
+    if getattr(a, "pm_steps", 0) > 0:
+        src = ("z=0 CIC density of a %d-step PM run of %d^3 particles (Zel'dovich ICs at z=100, "
+               "P~k^0.96 e^-k/5, sigma8=0.8, nDGP solve every step)" % (a.pm_steps, a.np))
+    else:
+        src = "CIC of %d^3 Zel'dovich particles (P~k^0.96 e^-k/5, sigma8=0.8, z=0)" % a.np
+    return ("nDGP FAS V(2,2) solve to eps/eps_ref<%g, %d^3 mesh, %s, L=%g Mpc/h, a=1, Omega_m=0.3, H0 rc=%g"
+            % (a.rtol, a.ng, src, a.box, a.rc))
 
 
 def run_reference(a, rank, world):
     if rank != 0:
         return
+    a.cpu_full_ng = 0   # each step is the bounded one-cycle sample only
     import numpy as np
     import oracle
     pos = particles(a, 0)
@@ -197,6 +270,9 @@ def run_reference(a, rank, world):
     dt = time.perf_counter() - t0
     v = float(np.mean(vals))
     cb["value"] = v
+    if a.pm_steps > 0:
+        cb["sample"] += ("; input: the Zel'dovich density at z = 0 of the same initial conditions (the "
+                         "%d-step particle-mesh run that evolves them is not part of the sample)" % a.pm_steps)
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
@@ -237,9 +313,61 @@ def main():
     for item in filter(None, a.fp32_shape.split(",")):
         ctx.set_fp32_smoother_shape(*(int(x) for x in item.split(":")))
     ng = a.ng
-    pos = torch.from_numpy(particles(a, rank)).to(dev)
+
+    def pm_run(rc, model=1, box=None):
+        """The particle-mesh run of the workload (Sec. 3.1 and 3.1.1): a.np^3
+        particles on the ng^3 mesh in a box of L Mpc/h, Zel'dovich initial
+        conditions at z = 100 on the growing mode (x = q + D psi,
+        p = a^2 E D f psi; seed 2 + rank), a.pm_steps leapfrog steps of
+        constant da to a = 1 (the first a half kick), FP32 particle state and,
+        for model 1, the FP64 nDGP solve (H0 r_c = rc, Sec. 3.2.3) at every
+        step to eps/eps_ref < rtol, warm-started from the previous step's
+        field.  Returns the z = 0 positions and the run's timings."""
+        import numpy as np
+        from paper_2110_00566_gb300 import inputs
+        box = box or a.box
+        a0, om = 1.0 / 101.0, 0.3
+        D, f = inputs.growth_lcdm(a0, om), inputs.growth_rate_lcdm(a0, om)
+        E0 = float(np.sqrt(om / a0 ** 3 + 1.0 - om))
+        p_, m_ = inputs.zeldovich(a.np, ng, box, inputs.pk_cutoff(0.96, 5.0, 0.8), D, seed=2 + rank,
+                                  vel_factor=a0 * a0 * E0 * f * D)
+        pos = torch.from_numpy(p_).to(dev)
+        mom = torch.from_numpy(m_).to(dev)
+        phi_ws = torch.zeros((ng, ng, ng), dtype=torch.float64, device=dev) if model else None
+        da = (1.0 - a0) / a.pm_steps
+        st = B.make_pm_state(pos, mom, ng, box, om, a0, da, model=model, rc_h0=rc, first=True, phi_ws=phi_ws)
+        o = B.opts(rtol=a.rtol, max_cycles=60)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cyc, solve_ms, warn = [], 0.0, 0
+        for _ in range(a.pm_steps):
+            rcode, sst = B.pm_step(ctx, st, o)
+            warn += int(rcode != 0)
+            if model:
+                cyc.append(sst.cycles)
+                solve_ms += sst.ms
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        res = {"steps": a.pm_steps, "particles": a.np ** 3, "ng": ng, "box_mpch": box, "z_start": 100.0,
+               "a_end": st.a, "model": ["GR", "nDGP", "Kmouflage"][model], "ms_total": ms,
+               "ms_per_step": ms / a.pm_steps, "precision": "FP32 particles" + (", FP64 solve" if model else "")}
+        if model:
+            res.update({"rc_h0": rc, "solve_ms_total": solve_ms, "solve_share": solve_ms / ms,
+                        "cycles_per_step_mean": float(np.mean(cyc)), "cycles_per_step_max": int(max(cyc)),
+                        "cycles_first_step": cyc[0], "steps_not_converged": warn,
+                        "warm_start": "previous step's field"})
+        return pos, res
+
+    pm_forms = {}
+    if a.pm_steps > 0:
+        pos, pm_forms["rc%g" % a.rc] = pm_run(a.rc)
+    else:
+        pos = torch.from_numpy(particles(a, rank)).to(dev)
     delta = torch.empty((ng, ng, ng), dtype=torch.float64, device=dev)
     B.pm_cic_deposit(ctx, ng, pos, delta)
+    del pos
     hbm_peak, peak_src = peaks()
 
     def reduce_max_sum(x, y):
@@ -309,6 +437,9 @@ def main():
     TRAFFIC = {"fp64": (1616.1e6 + 524.6e6, 512), "mixed": (1673.9e6 + 255.5e6, 512)}
 
     def roofline(r, precision, fp64_tf):
+        """Roofline of the finest half-sweep, anchored to the HBM peak (the
+        metric's "% of HBM peak"): achieved = the algorithmic bytes of one
+        launch over its average CUDA-event duration in the timed solves."""
         ms = r["avg_launch_ms"]
         tb, tn = TRAFFIC[precision]
         traffic = tb * (ng / float(tn)) ** 3
@@ -316,11 +447,11 @@ def main():
             tn, "" if tn == ng else ", scaled by (ng/%d)^3" % tn)
         if precision == "fp64":
             # finest FP64 half-sweep: read both colours + the colour's s,
-            # write the colour = 2 s n^3 bytes (s = 8).  Bound by its
-            # arithmetic pipes: the peak is the speed of light of its
-            # instruction mix (the busiest pipe's issue time at the sampled SM
-            # clock), and the FP64-only view compares the algorithmic flops
-            # with the FP64 peak an all-FP64 kernel is held to
+            # write the colour = 2 s n^3 bytes (s = 8).  Its limiter is the
+            # arithmetic pipes, not HBM: the instruction-mix speed of light
+            # (the busiest pipe's issue time at the sampled SM clock) and the
+            # algorithmic FP64 flops against the FP64 FMA rate are reported
+            # beside the HBM fraction as diagnostics
             cells = ng ** 3 / 2
             alg = 2 * 8 * ng ** 3
             gbs = alg / (ms * 1e-3) / 1e9
@@ -332,19 +463,16 @@ def main():
                    "fma": FP64_MIX["fma"] / PIPE_RATE["fma"], "issue": FP64_MIX["issue"] / PIPE_RATE["issue"]}
             bind = max(cyc, key=cyc.get)
             t_sol = cells / nsm * cyc[bind] / (mhz * 1e6)
-            peak = FLOPS_PER_CELL_FP64 * cells / t_sol / 1e12
-            return {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+            return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                     "traffic": traffic, "traffic_source": tsrc, "kernel": "k_smooth2<double> finest half-sweep",
-                    "peak_source": "speed of light of the kernel's instruction mix: busiest pipe (%s) at %d "
-                                   "instructions/clock/SM, %.0f MHz, %d SMs" % (
-                                       bind, PIPE_RATE.get(bind, rate64), mhz, nsm),
-                    "alg_flops_per_cell": FLOPS_PER_CELL_FP64, "avg_launch_ms": ms, "launches": r["fine_launches"],
-                    "sol_ms_per_launch": t_sol * 1e3, "binding_pipe": bind,
-                    "instructions_per_cell": FP64_MIX, "sm_clocks_per_cell": cyc,
-                    "fp64_only_view": {"achieved": tf, "peak": fp64_tf, "unit": "TFLOP/s", "frac": tf / fp64_tf,
-                                       "peak_source": "FP64 FMA rate measured by mg_probe_alu_peaks on this GPU"},
-                    "hbm_view": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                                 "alg_bytes_per_launch": alg, "peak_source": peak_src}}
+                    "peak_source": peak_src + " HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "alg_bytes_per_launch": alg, "avg_launch_ms": ms, "launches": r["fine_launches"],
+                    "limiter": "integer ALU and FP64 issue (instruction mix), not HBM",
+                    "alu_view": {"achieved": tf, "unit": "TFLOP/s", "alg_flops_per_cell": FLOPS_PER_CELL_FP64,
+                                 "fp64_fma_peak": fp64_tf, "frac_of_fp64_fma_peak": tf / fp64_tf,
+                                 "instruction_mix_sol_ms": t_sol * 1e3, "frac_of_instruction_mix_sol": t_sol * 1e3 / ms,
+                                 "binding_pipe": bind, "instructions_per_cell": FP64_MIX,
+                                 "sm_clocks_per_cell": cyc, "sm_mhz": mhz}}
         # finest FP32 correction half-sweep: read e and the base field (both
         # colours, 4 B each), s and f of the colour (2 B each), write the
         # colour (2 B) = 14 n^3 bytes
@@ -354,6 +482,46 @@ def main():
                 "traffic": traffic, "traffic_source": tsrc, "kernel": "k_smooth4<float, correction, nDGP> finest half-sweep",
                 "peak_source": peak_src, "avg_launch_ms": ms, "launches": r["fine_launches"],
                 "alg_bytes_per_launch": alg}
+
+    def at_accuracy(dl, rc, tol=1e-6):
+        """The FP64 and mixed-precision solves at the same accuracy: the
+        loosest rtol in {1e-4 ... 1e-8} whose phi lies within tol (relative
+        L2) of a tight FP64 solution (rtol 1e-12), each timed over a.steps
+        solves from phi = 0."""
+        inst = dict(ng=ng, box_mpch=a.box, a=1.0, omega_m=0.3, rc_h0=rc, delta=dl)
+        ref = torch.zeros_like(dl)
+        B.mg_solve_dgp(ctx, [dict(inst, phi=ref)], B.opts(rtol=1e-12, max_cycles=60))
+        nref = torch.linalg.vector_norm(ref)
+        out = {"tolerance": tol, "reference": "FP64 solve to eps/eps_ref < 1e-12"}
+        for name, prec in (("fp64", B.MG_PREC_FP64), ("mixed", B.MG_PREC_MIXED)):
+            phi = torch.zeros_like(dl)
+            pick = None
+            for rt in (1e-4, 1e-5, 1e-6, 1e-7, 1e-8):
+                o = B.opts(rtol=rt, precision=prec, max_cycles=60)
+                phi.zero_()
+                B.mg_solve_dgp(ctx, [dict(inst, phi=phi)], o)
+                err = float(torch.linalg.vector_norm(phi - ref) / nref)
+                if err <= tol:
+                    pick = (rt, err, o)
+                    break
+            if pick is None:
+                out[name] = {"reached": False}
+                continue
+            rt, err, o = pick
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            cyc = 0
+            for _ in range(a.steps):
+                _, st = B.mg_solve_dgp(ctx, [dict(inst, phi=phi)], o)
+                cyc = st[0].cycles
+            e1.record()
+            torch.cuda.synchronize(dev)
+            out[name] = {"rtol": rt, "phi_rel_l2_vs_tight": err, "ms": e0.elapsed_time(e1) / a.steps,
+                         "cycles": cyc}
+        if "ms" in out.get("fp64", {}) and "ms" in out.get("mixed", {}):
+            out["mixed_speedup"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+        return out
 
     def batched():
         """Emulator ensemble: a.batch independent solves, N uniform over
@@ -419,11 +587,50 @@ def main():
         worst64 = max(float(torch.linalg.vector_norm(x["phi"] - y["phi"]) / torch.linalg.vector_norm(y["phi"]))
                       for x, y in zip(insts, seq64))
         cells = sum(x["ng"] ** 3 for x in insts)
+        # at the same accuracy: the loosest rtol at which every instance's phi
+        # lies within 1e-6 (relative L2) of its tight FP64 solution, for the
+        # batched call and for the loop of plain FP64 solves
+        tight = [torch.zeros_like(x["delta"]) for x in insts]
+        for x, t in zip(insts, tight):
+            B.mg_solve_dgp(ctx, [dict(x, phi=t)], B.opts(rtol=1e-12, max_cycles=60))
+
+        def worst_vs_tight(phis):
+            return max(float(torch.linalg.vector_norm(p - t) / torch.linalg.vector_norm(t))
+                       for p, t in zip(phis, tight))
+
+        acc = {"tolerance": 1e-6}
+        for rt in (1e-5, 1e-6, 1e-7, 1e-8):
+            ob = B.opts(rtol=rt, precision=B.MG_PREC_MIXED, max_cycles=60)
+            B.mg_solve_dgp(ctx, insts, ob)
+            wb = worst_vs_tight([x["phi"] for x in insts])
+            if wb <= 1e-6:
+                torch.cuda.synchronize(dev)
+                e0.record()
+                B.mg_solve_dgp(ctx, insts, ob)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                acc["batched"] = {"rtol": rt, "ms": e0.elapsed_time(e1), "phi_worst_rel_l2_vs_tight": wb}
+                break
+        for rt in (1e-5, 1e-6, 1e-7, 1e-8):
+            o64r = B.opts(rtol=rt, precision=B.MG_PREC_FP64, max_cycles=60)
+            torch.cuda.synchronize(dev)
+            e0.record()
+            for inst in seq64:
+                B.mg_solve_dgp(ctx, [inst], o64r)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            w64 = worst_vs_tight([x["phi"] for x in seq64])
+            if w64 <= 1e-6:
+                acc["fp64_loop"] = {"rtol": rt, "ms": e0.elapsed_time(e1), "phi_worst_rel_l2_vs_tight": w64}
+                break
+        if "batched" in acc and "fp64_loop" in acc:
+            acc["speedup_vs_fp64_loop"] = acc["fp64_loop"]["ms"] / acc["batched"]["ms"]
         return {"value": upd / a.steps / (ms_b * 1e-3) / 1e9, "unit": UNIT, "instances": a.batch,
                 "total_cells": cells, "ms_per_batch": ms_b, "ms_sequential_loop": ms_s,
                 "speedup_vs_sequential": ms_s / ms_b, "phi_rel_l2_vs_sequential_max": worst,
                 "ms_fp64_loop": ms_64, "speedup_vs_fp64_loop": ms_64 / ms_b, "phi_rel_l2_vs_fp64_max": worst64,
-                "sizes": sorted({x["ng"] for x in insts}), "launch": "one persistent cooperative kernel, graph-captured"}
+                "sizes": sorted({x["ng"] for x in insts}), "launch": "one persistent cooperative kernel, graph-captured",
+                "at_equal_accuracy": acc}
 
     def adjoint():
         """Backward/forward: the FP64 adjoint solve (mg_solve_adjoint) vs the
@@ -458,20 +665,23 @@ def main():
         return {"ng": n, "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
                 "adjoint_cycles": cyc, "precision": "fp64"}
 
-    def kmouflage():
-        """Kmouflage solves on the headline mesh with a 512 Mpc/h box (the
-        same Zel'dovich load, seed 3): (n, K0) = (2, 1) and (3, 1),
-        beta = 0.2, a = 1, with lambda, phibar'/H0 and A(phibar) from the
-        library's background solve of each model; the FP64 solve and the
-        mixed-precision solve, the latter's phi against the former's (both
-        to rtol)."""
+    def kmouflage(pos_z0=None):
+        """Kmouflage solves on the headline mesh with a 512 Mpc/h box: the
+        z = 0 density of the same seeded run in that box (GR dynamics), or
+        without a run the Zel'dovich load at z = 0 (seed 3); (n, K0) =
+        (2, 1) and (3, 1), beta = 0.2, a = 1, with lambda, phibar'/H0 and
+        A(phibar) from the library's background solve of each model; the
+        FP64 solve and the mixed-precision solve, the latter's phi against
+        the former's (both to rtol)."""
         import numpy as np
         from paper_2110_00566_gb300 import inputs
         box = 2.0 * a.box
-        pk = inputs.pk_cutoff(0.96, 5.0, 0.8)
-        p_, _ = inputs.zeldovich(a.np, ng, box, pk, 1.0, seed=3)
+        if pos_z0 is None:
+            pk = inputs.pk_cutoff(0.96, 5.0, 0.8)
+            p_, _ = inputs.zeldovich(a.np, ng, box, pk, 1.0, seed=3)
+            pos_z0 = torch.from_numpy(p_).to(dev)
         dk = torch.empty((ng, ng, ng), dtype=torch.float64, device=dev)
-        B.pm_cic_deposit(ctx, ng, torch.from_numpy(p_).to(dev), dk)
+        B.pm_cic_deposit(ctx, ng, pos_z0, dk)
         out = {}
         for nk, k0 in ((2, 1.0), (3, 1.0)):
             t0 = time.perf_counter()
@@ -605,11 +815,42 @@ def main():
     second = None
     if not a.no_forms:
         second = timed("mixed" if a.precision == "fp64" else "fp64")
+    acc_form = at_accuracy(delta, a.rc) if not a.no_forms else None
+    rc5_form = None
+    if not a.no_forms and a.pm_steps > 0 and a.rc != 5.0:
+        # the run and the headline solve at H0 r_c = 5: its own z = 0 density
+        pos5, pm_forms["rc5"] = pm_run(5.0)
+        d5 = torch.empty_like(delta)
+        B.pm_cic_deposit(ctx, ng, pos5, d5)
+        del pos5
+        rc5_form = {}
+        for name, prec in (("fp64", B.MG_PREC_FP64), ("mixed", B.MG_PREC_MIXED)):
+            o5 = B.opts(rtol=a.rtol, precision=prec, max_cycles=60)
+            i5 = dict(ng=ng, box_mpch=a.box, a=1.0, omega_m=0.3, rc_h0=5.0, delta=d5, phi=torch.zeros_like(d5))
+            B.mg_solve_dgp(ctx, [i5], o5)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            upd = 0
+            for _ in range(a.steps):
+                _, st5 = B.mg_solve_dgp(ctx, [i5], o5)
+                upd += st5[0].cell_updates
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms5 = e0.elapsed_time(e1)
+            rc5_form[name] = {"value": upd / (ms5 * 1e-3) / 1e9, "unit": UNIT, "ms_per_solve": ms5 / a.steps,
+                              "cycles": st5[0].cycles,
+                              "final_eps_over_eps_ref": st5[0].eps[st5[0].n_eps - 1] / st5[0].eps_ref}
+        del d5
+    kmo_pos = None
+    if not a.no_forms and a.pm_steps > 0:
+        kmo_pos, pm_forms["gr_512mpch"] = pm_run(0.0, model=0, box=2.0 * a.box)
     e2e_primary = None if a.no_e2e else e2e(primary)
     batch_form = batched() if (a.batch > 0 and not a.no_forms) else None
     adj_form = adjoint() if (a.adj_ng > 0 and not a.no_forms) else None
     pm_adj_form = adjoint_pm() if (a.pm_adj_ng > 0 and not a.no_forms) else None
-    kmo_form = kmouflage() if not a.no_forms else None
+    kmo_form = kmouflage(kmo_pos) if not a.no_forms else None
+    kmo_pos = None
     cyc_form = cycle_types() if not a.no_forms else None
 
     if rank != 0:
@@ -641,6 +882,12 @@ def main():
         forms["kmouflage"] = kmo_form
     if cyc_form is not None:
         forms["cycle_types"] = cyc_form
+    if acc_form is not None:
+        forms["at_equal_accuracy"] = acc_form
+    if rc5_form is not None:
+        forms["rc5"] = rc5_form
+    if pm_forms:
+        forms["pm_run"] = pm_forms
     cb = None if a.no_cpu else cpu_baseline(delta.cpu().numpy(), a)
     line = {"metric": METRIC, "value": primary["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": primary["ms_per_step"], "higher_is_better": True,
@@ -659,6 +906,7 @@ def main():
             "e2e": e2e_primary,
             "cpu_baseline": cb,
             "forms": forms}
+    line["forms_summary"] = summarise(line, primary)
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
