@@ -103,10 +103,15 @@ int mg_probe_alu_peaks(mg_ctx *ctx, double *fp64_tflops, double *fp32_tflops);
  *           quotient; relative error below 2^-43 for positive normal x below
  *           2^1022),
  *   fn = 2: N(Sigma) of Eq. DGP, the Vainshtein term, at Sigma = x[q] for the
- *           given alpha, N = (3/4)[-alpha + sgn(alpha) sqrt(alpha^2 + 8 Sigma/3)]
- *           in the rationalised form 2 sgn(alpha) Sigma / (|alpha| + sqrt(...))
- *           that the kernels evaluate (a cell with Q = 0 and density term
- *           Sigma; arguments below zero give -(3/4) alpha).
+ *           given alpha, N = (3/4)[-alpha + sgn(alpha) sqrt(alpha^2 + 8 Sigma/3)],
+ *           as the kernels evaluate it (a cell with Q = 0 and density term
+ *           Sigma): an FP32 estimate of the rationalised form
+ *           2 sgn(alpha) Sigma / (|alpha| + sqrt(...)) refined by one FP64
+ *           Newton step on Eq. dgp_quadratic_eom, (2/3) N^2 + alpha N = Sigma
+ *           (relative error about 2^-44 where the root's square root is at
+ *           least |alpha|/2), else the rationalised form in FP64 with the
+ *           square root and reciprocal of fn 0 and 1 (arguments below zero
+ *           give -(3/4) alpha).
  * x, y: device arrays of n doubles on the context's device (host pointers
  * are rejected); alpha: finite and nonzero (read for fn = 2 only).  Queued
  * on the context's stream.  Errors: MG_ERR_ARG, MG_ERR_CUDA.  (The paper has
@@ -443,6 +448,17 @@ typedef struct {
 int dpm_run(mg_ctx *ctx, const dpm_config *cfg, const mg_opts *opts, const double *amp,
             const double *noise, double rc_h0, const double *target_pk, double *pk_out,
             double *loss_out, double *dL_dnoise_out, double *dL_drc_out, mg_stats *stats);
+
+/* The vector-Jacobian product of the run for any loss of the caller's on
+ * P: the forward run (P written to pk_out, HOST, nbins) and the reverse pass
+ * seeded with dL_dpk (HOST, nbins: dL/dP_b) instead of the built-in loss's
+ * 2 (P_b - target_b) / nbins, giving dL/dw (ng^3) and, when dL_drc_out
+ * (HOST) is given, dL/dR_c (0 for GR).  The forward run is deterministic, so
+ * a forward call with dpm_run and this call see the same P.  Errors as
+ * dpm_run; dL_dpk and dL_dnoise_out must not be NULL. */
+int dpm_run_vjp(mg_ctx *ctx, const dpm_config *cfg, const mg_opts *opts, const double *amp,
+                const double *noise, double rc_h0, const double *dL_dpk, double *pk_out,
+                double *dL_dnoise_out, double *dL_drc_out, mg_stats *stats);
 
 /* The pieces, each with its adjoint (vector-Jacobian product), for
  * checking.  dpm_ic: positions and momenta from noise; dpm_ic_adjoint:

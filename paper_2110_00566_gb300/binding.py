@@ -121,6 +121,8 @@ def _declare(L):
                                        _VP, _P(mg_stats)]),
         "dpm_run": (C.c_int, [_VP, _P(dpm_config), _P(mg_opts), _VP, _VP, C.c_double, _VP, _VP, _VP, _VP, _VP,
                               _P(mg_stats)]),
+        "dpm_run_vjp": (C.c_int, [_VP, _P(dpm_config), _P(mg_opts), _VP, _VP, C.c_double, _VP, _VP, _VP, _VP,
+                                  _P(mg_stats)]),
         "dpm_ic": (C.c_int, [_VP, _P(dpm_config), _VP, _VP, _VP, _VP]),
         "dpm_ic_adjoint": (C.c_int, [_VP, _P(dpm_config), _VP, _VP, _VP, _VP]),
         "dpm_deposit": (C.c_int, [_VP, C.c_int, _VP, C.c_longlong, _VP]),
@@ -434,6 +436,24 @@ def dpm_run(ctx: Context, cfg: dpm_config, amp, noise, rc_h0, target=None, dnois
             drc.value if (dnoise_out is not None and want_drc) else None, st)
 
 
+def dpm_run_vjp(ctx: Context, cfg: dpm_config, amp, noise, rc_h0, dpk, dnoise_out, want_drc=True,
+                o: mg_opts = None):
+    """Forward run and the reverse pass seeded with dL/dP = dpk (nbins).
+    Returns (P (nbins,), dL/dR_c or None, stats); dL/dw goes to dnoise_out."""
+    _check_dtype(amp, "f64")
+    _check_dtype(noise, "f64")
+    _check_dtype(dnoise_out, "f64")
+    pk = np.zeros(cfg.nbins)
+    g = _host_f64(dpk, cfg.nbins)
+    drc = C.c_double(0.0)
+    st = mg_stats()
+    rc = lib().dpm_run_vjp(ctx.h, C.byref(cfg), C.byref(o or opts()), _ptr(amp), _ptr(noise), float(rc_h0),
+                           g.ctypes.data, pk.ctypes.data, _ptr(dnoise_out),
+                           C.cast(C.pointer(drc), C.c_void_p) if want_drc else None, C.byref(st))
+    ctx._rc(rc)
+    return pk, (drc.value if want_drc else None), st
+
+
 def dpm_ic(ctx: Context, cfg: dpm_config, amp, noise, pos_out, mom_out):
     for x in (amp, noise, pos_out, mom_out):
         _check_dtype(x, "f64")
@@ -557,3 +577,35 @@ def autograd_solve():
             return out, torch.tensor(drc, dtype=torch.float64), None, None, None, None, None
 
     return MGSolveFn
+
+
+def autograd_pm():
+    """torch.autograd.Function over the differentiable particle-mesh run:
+    forward gives the binned power spectrum P (nbins, FP64, on the noise
+    tensor's device) from the white noise and R_c by dpm_run; backward calls
+    dpm_run_vjp with the incoming dL/dP, so any loss of the caller's on P
+    differentiates with respect to the noise and R_c.  Usage:
+        pk = autograd_pm().apply(noise, rc, ctx, cfg, amp, opts)
+    with noise a CUDA FP64 tensor (ng^3), rc a 0-d FP64 tensor and amp the
+    rfft-grid amplitudes of dpm_run."""
+    import torch
+
+    class PMRunFn(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, noise, rc, mgctx, cfg, amp, o):
+            noise = noise.contiguous()
+            pk, _, _, _ = dpm_run(mgctx, cfg, amp, noise, float(rc), o=o)
+            fctx.save_for_backward(noise)
+            fctx.args = (mgctx, cfg, amp, float(rc), o, rc.device if torch.is_tensor(rc) else None)
+            return torch.from_numpy(pk).to(noise.device)
+
+        @staticmethod
+        def backward(fctx, gpk):
+            (noise,) = fctx.saved_tensors
+            mgctx, cfg, amp, rc, o, rdev = fctx.args
+            dn = torch.empty_like(noise)
+            _, drc, _ = dpm_run_vjp(mgctx, cfg, amp, noise, rc, gpk.detach().double().cpu().numpy(), dn, o=o)
+            grc = torch.tensor(drc, dtype=torch.float64, device=rdev) if rdev is not None else None
+            return dn, grc, None, None, None, None
+
+    return PMRunFn

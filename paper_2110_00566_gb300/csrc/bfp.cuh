@@ -1,0 +1,246 @@
+// Block fixed-point staging of the FP64 nDGP kernels: a block owns a tile of
+// 32 split-index columns by 8 rows of one level and walks consecutive planes;
+// a ring of three planes (both colour arrays, the tile plus its one-cell
+// halo) holds the level's values in shared memory converted once to the
+// fixed-point integers of fixsum.cuh, so that the 19-point stencil's signed
+// sums and quadratic form are formed from shared-memory integers with no
+// per-use conversion.
+//
+// Scale.  The three staged planes share one scale, the largest exponent field
+// E among their values (each plane's maximum over the tile and its halo, both
+// colours, is kept): x = M 2^(e - 1075) becomes sign(x) floor(M 2^6 / 2^(E - e)),
+// exact when E - e <= 6 and otherwise within 2^(E - 1081), 1/64 of an ulp of
+// the largest value of the three planes.  When the next plane raises E the
+// staged planes are shifted down to it (sign and magnitude: exactly the
+// values a direct conversion at the new scale gives); when E falls by more
+// than two binades they are converted again from their FP64 values, kept in a
+// second ring, so that the scale never exceeds the local largest value by
+// more than 2^2.  Outside the fixed-point domain (fx_ok: a value above 2^506,
+// NaN or infinity) the caller evaluates those planes' cells in FP64.
+//
+// Use: construct, fill(i0), then per plane i: prefetch(i + 2) before the
+// update of plane i, the update (slots sm, s0, sp hold planes i - 1, i, i + 1),
+// and advance(step) after it.  Every thread of the block must make the same
+// calls (they contain barriers).
+#pragma once
+#include "fixsum.cuh"
+
+namespace mg {
+namespace bfp {
+
+constexpr int TM = 32;                  // split-index columns per tile
+constexpr int TJ = 8;                   // rows per tile
+constexpr int W = TM + 2;               // the tile with the k+-1 halo columns
+constexpr int H = TJ + 2;               // and the j+-1 halo rows
+constexpr int PLANE = W * H;            // values per colour and plane
+constexpr int LOAD = 2 * PLANE;         // values staged per plane (both colours)
+constexpr int THREADS = TM * TJ;
+constexpr int PER = (LOAD + THREADS - 1) / THREADS;
+
+struct Shared {
+    long long v[3][LOAD];   // slot -> [colour][row][column]
+    double raw[3][LOAD];    // the same values in FP64
+    int pmax[3];            // each slot's largest exponent field
+    int emax[2];            // block maximum of a plane being reduced (double-buffered)
+};
+
+// sign-and-magnitude shift to a coarser scale: the truncation toward zero of
+// the conversion itself
+__device__ __forceinline__ long long down(long long v, unsigned d)
+{
+    if (d >= 63) return 0;
+    const long long a = v < 0 ? -v : v;
+    const long long r = a >> d;
+    return v < 0 ? -r : r;
+}
+
+__device__ __forceinline__ int ef_of(double x) { return __double2hiint(x) & 0x7FF00000; }
+
+// the value of colour slot c (0: A0, 1: A1) at tile row r, column col
+__device__ __forceinline__ long long at(const long long *slot, int c, int r, int col)
+{
+    return slot[c * PLANE + r * W + col];
+}
+
+struct Stager {
+    Shared &t;
+    const double *A0, *A1;   // the colour arrays staged as colour slots 0 and 1
+    int n, tid;
+    long long pstride;
+    int goff[PER];
+    unsigned ocol;           // bit q: element q comes from A1
+    double x[PER];           // a plane in flight
+    int E = 0;               // the staged planes' largest exponent field (0: all zero)
+    int ef = 1023 << 20;     // the conversion scale
+    int sm = 0, s0 = 1, sp = 2;
+
+    // element e = tid + q * THREADS of a plane is colour e / PLANE, tile row
+    // jj, column mm: row j0 - 1 + jj and split index m0 - 1 + mm (wrapped)
+    __device__ Stager(Shared &sh, const double *a0, const double *a1, int n_, int half, int m0, int j0, int tid_)
+        : t(sh), A0(a0), A1(a1), n(n_), tid(tid_), pstride((long long)n_ * half), ocol(0)
+    {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * THREADS;
+            const int ee = e < LOAD ? e : 0;
+            const int col = ee >= PLANE;
+            const int r = ee - col * PLANE;
+            const int jj = r / W, mm = r - jj * W;
+            int j = j0 - 1 + jj, m = m0 - 1 + mm;
+            j = j < 0 ? j + n : (j >= n ? j - n : j);
+            m = m < 0 ? m + half : (m >= half ? m - half : m);
+            goff[q] = j * half + m;
+            ocol |= (unsigned)col << q;
+        }
+    }
+    __device__ int wrap(int i) const { return i < 0 ? i + n : (i >= n ? i - n : i); }
+    __device__ void prefetch(int ip)
+    {
+        const long long base = (long long)wrap(ip) * pstride;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * THREADS;
+            x[q] = e < LOAD ? __ldg(((ocol >> q) & 1 ? A1 : A0) + base + goff[q]) : 0.0;
+        }
+    }
+    __device__ int xmax() const
+    {
+        int e = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) e = max(e, ef_of(x[q]));
+        return e;
+    }
+    __device__ void block_max(int slot, int e)
+    {
+        e = __reduce_max_sync(0xffffffffu, e);
+        if ((tid & 31) == 0) atomicMax(&t.emax[slot], e);
+    }
+    __device__ void store(int s)
+    {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * THREADS;
+            if (e < LOAD) {
+                t.raw[s][e] = x[q];
+                t.v[s][e] = fx_in<6>(x[q], ef);
+            }
+        }
+    }
+    __device__ void shift_down(int s, unsigned d)
+    {
+        for (int e = tid; e < LOAD; e += THREADS) t.v[s][e] = down(t.v[s][e], d);
+    }
+    __device__ void reconvert(int s)
+    {
+        for (int e = tid; e < LOAD; e += THREADS) t.v[s][e] = fx_in<6>(t.raw[s][e], ef);
+    }
+    // planes i0 - 1, i0, i0 + 1 into slots 0, 1, 2; each plane's maximum is
+    // reduced on its own (reduction slot q & 1; the other slot, read before
+    // the previous barrier, is cleared between this plane's two barriers)
+    __device__ void fill(int i0)
+    {
+        if (tid == 0) {
+            t.emax[0] = 0;
+            t.emax[1] = 0;
+        }
+        __syncthreads();
+        double xs[2][PER];
+        for (int q3 = 0; q3 < 3; ++q3) {
+            prefetch(i0 + q3 - 1);
+            block_max(q3 & 1, xmax());
+            __syncthreads();
+            const int e3 = t.emax[q3 & 1];
+            if (tid == 0) {
+                t.pmax[q3] = e3;
+                t.emax[(q3 + 1) & 1] = 0;
+            }
+            __syncthreads();
+            E = max(E, e3);
+            if (q3 < 2) {
+#pragma unroll
+                for (int q = 0; q < PER; ++q) xs[q3][q] = x[q];
+            }
+        }
+        ef = fx_zero_scale(E);
+        store(2);
+#pragma unroll
+        for (int q = 0; q < PER; ++q) x[q] = xs[0][q];
+        store(0);
+#pragma unroll
+        for (int q = 0; q < PER; ++q) x[q] = xs[1][q];
+        store(1);
+        if (tid == 0) t.emax[0] = 0;   // slot 0, last read before the fill's final barrier
+        __syncthreads();
+        sm = 0;
+        s0 = 1;
+        sp = 2;
+    }
+    // stage the prefetched plane into the slot of the oldest plane, at the
+    // scale of the new triple, and rotate the slots (step counts from 0)
+    __device__ void advance(int step)
+    {
+        block_max(step & 1, xmax());
+        __syncthreads();
+        const int en = t.emax[step & 1];
+        const int Et = max(max(t.pmax[s0], t.pmax[sp]), en);
+        if (Et > E) {
+            if (E != 0) {
+                const unsigned d = (unsigned)(Et - E) >> 20;
+                shift_down(s0, d);
+                shift_down(sp, d);
+            }
+            E = Et;
+            ef = fx_zero_scale(E);
+        } else if (Et < E - (2 << 20)) {
+            E = Et;
+            ef = fx_zero_scale(E);
+            reconvert(s0);
+            reconvert(sp);
+        }
+        store(sm);
+        if (tid == 0) {
+            t.pmax[sm] = en;
+            t.emax[(step + 1) & 1] = 0;
+        }
+        __syncthreads();
+        const int o = s0;
+        s0 = sp;
+        sp = sm;
+        sm = o;
+    }
+};
+
+// the 19-point stencil of the colour-c cell at tile row jj, column mm of
+// plane i (row parity p = (c + i + j) & 1) from the staged integers: the
+// face sums X, Y, Z (S6 = X + Y + Z) and the mixed differences C_xy, C_xz,
+// C_yz; slot colour c is the cell's own array, 1 - c the other
+struct Sums {
+    long long X, Y, Z, cxy, cxz, cyz;
+};
+__device__ __forceinline__ Sums stencil(const long long *Sm, const long long *S0, const long long *Sp, int c, int jj,
+                                        int mm, int p)
+{
+    const int o = 1 - c;
+    Sums r;
+    r.X = at(Sp, o, jj, mm) + at(Sm, o, jj, mm);
+    r.Y = at(S0, o, jj + 1, mm) + at(S0, o, jj - 1, mm);
+    r.Z = at(S0, o, jj, mm + p) + at(S0, o, jj, mm + p - 1);
+    r.cxy = (at(Sp, c, jj + 1, mm) + at(Sm, c, jj - 1, mm)) - (at(Sp, c, jj - 1, mm) + at(Sm, c, jj + 1, mm));
+    r.cxz = (at(Sp, c, jj, mm + p) + at(Sm, c, jj, mm + p - 1)) - (at(Sp, c, jj, mm + p - 1) + at(Sm, c, jj, mm + p));
+    r.cyz = (at(S0, c, jj + 1, mm + p) + at(S0, c, jj - 1, mm + p - 1)) -
+            (at(S0, c, jj + 1, mm + p - 1) + at(S0, c, jj - 1, mm + p));
+    return r;
+}
+
+// Q16 = 16 (a (a - b) + b^2) + 3 (C_xy^2 + C_xz^2 + C_yz^2), exact in 128 bits
+// (a = X - Y, b = X - Z), rounded once to binary64 at the scale ef
+__device__ __forceinline__ double quad(const Sums &r, int ef)
+{
+    const long long a = r.X - r.Y, b = r.X - r.Z, amb = r.Z - r.Y;
+    const U128 Eh = add128(mul_s64(a, amb), sqr_s64(b));
+    const U128 C = add128(add128(sqr_s64(r.cxy), sqr_s64(r.cxz)), sqr_s64(r.cyz));
+    return fx_out_q(add128(shl128(Eh, 4), add128(C, shl128(C, 1))), ef);
+}
+
+}  // namespace bfp
+}  // namespace mg

@@ -676,16 +676,20 @@ using namespace mg;
 
 extern "C" {
 
-int dpm_run(mg_ctx *ctx, const dpm_config *cfg, const mg_opts *opts, const double *amp, const double *noise,
-            double rc_h0, const double *target_pk, double *pk_out, double *loss_out, double *dL_dnoise_out,
-            double *dL_drc_out, mg_stats *stats)
+// the forward run and, with dL_dnoise_out, the reverse pass seeded with the
+// cotangent of P: dL/dP_b = 2 (P_b - target_b) / nbins of the built-in loss
+// (target_pk), or the caller's dpk_in
+static int run_impl(mg_ctx *ctx, const dpm_config *cfg, const mg_opts *opts, const double *amp, const double *noise,
+                    double rc_h0, const double *target_pk, const double *dpk_in, double *pk_out, double *loss_out,
+                    double *dL_dnoise_out, double *dL_drc_out, mg_stats *stats)
 {
     if (!ctx) return MG_ERR_ARG;
     int rc = check_cfg(ctx, cfg, true);
     if (rc) return rc;
     if (!amp || !noise || !pk_out) return set_err(ctx, MG_ERR_ARG, "null amp, noise or pk_out");
     if (cfg->model == 1 && !(rc_h0 > 0)) return set_err(ctx, MG_ERR_ARG, "rc_h0 must be > 0");
-    if (dL_dnoise_out && !target_pk) return set_err(ctx, MG_ERR_ARG, "the gradient needs target_pk");
+    if (dL_dnoise_out && !target_pk && !dpk_in)
+        return set_err(ctx, MG_ERR_ARG, "the gradient needs target_pk or dL/dP");
     mg_opts o;
     if (opts)
         o = *opts;
@@ -735,7 +739,8 @@ int dpm_run(mg_ctx *ctx, const dpm_config *cfg, const mg_opts *opts, const doubl
         }
         if (dgrad) {
             std::vector<double> dpk(c.nbins);
-            for (int b = 0; b < c.nbins; ++b) dpk[b] = 2.0 * (pk_out[b] - target_pk[b]) / c.nbins;
+            for (int b = 0; b < c.nbins; ++b)
+                dpk[b] = dpk_in ? dpk_in[b] : 2.0 * (pk_out[b] - target_pk[b]) / c.nbins;
             power_spectrum_adjoint(ctx, w, n, c.box_mpch, c.nbins, w.delta, dpk.data(), counts.data(), w.dd);
             k_dep64_adj<<<gridp(cells), 256, 0, s>>>(w.x, cells, n, w.dd, 1.0, w.xb, 0);
             MG_CK(cudaMemsetAsync(w.pb, 0, pb, s));
@@ -767,6 +772,24 @@ int dpm_run(mg_ctx *ctx, const dpm_config *cfg, const mg_opts *opts, const doubl
     }
     if (stats) *stats = loc;
     return rc;
+}
+
+int dpm_run(mg_ctx *ctx, const dpm_config *cfg, const mg_opts *opts, const double *amp, const double *noise,
+            double rc_h0, const double *target_pk, double *pk_out, double *loss_out, double *dL_dnoise_out,
+            double *dL_drc_out, mg_stats *stats)
+{
+    return run_impl(ctx, cfg, opts, amp, noise, rc_h0, target_pk, nullptr, pk_out, loss_out, dL_dnoise_out,
+                    dL_drc_out, stats);
+}
+
+int dpm_run_vjp(mg_ctx *ctx, const dpm_config *cfg, const mg_opts *opts, const double *amp, const double *noise,
+                double rc_h0, const double *dL_dpk, double *pk_out, double *dL_dnoise_out, double *dL_drc_out,
+                mg_stats *stats)
+{
+    if (!ctx) return MG_ERR_ARG;
+    if (!dL_dpk || !dL_dnoise_out) return set_err(ctx, MG_ERR_ARG, "null dL_dpk or dL_dnoise_out");
+    return run_impl(ctx, cfg, opts, amp, noise, rc_h0, nullptr, dL_dpk, pk_out, nullptr, dL_dnoise_out, dL_drc_out,
+                    stats);
 }
 
 int dpm_ic(mg_ctx *ctx, const dpm_config *cfg, const double *amp, const double *noise, double *pos_out,

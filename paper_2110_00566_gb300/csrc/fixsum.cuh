@@ -156,6 +156,26 @@ __device__ __forceinline__ U128 shl128(U128 x, int k)  // 0 < k < 64
     return r;
 }
 
+// x^2 as an unsigned 128-bit integer (|x| < 2^63)
+__device__ __forceinline__ U128 sqr_s64(long long x)
+{
+    const unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    U128 r;
+    r.lo = a * a;
+    r.hi = __umul64hi(a, a);
+    return r;
+}
+
+// trunc(x / 6) for |x| < 2^63 without a division: floor(a / 6) =
+// floor(a (2^65 + 1) / 3 / 2^66) for a < 2^64, because a / (3 2^66) < 1/24 and
+// the fractional part of a / 6 is at most 5/6
+__device__ __forceinline__ long long fx_div6(long long x)
+{
+    const unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    const long long q = (long long)(__umul64hi(a, 0xAAAAAAAAAAAAAAABull) >> 2);
+    return x < 0 ? -q : q;
+}
+
 // Q (an unsigned 128-bit integer at the squared scale of exponent field ef,
 // in place) to binary64, rounded once to nearest (ties away from zero)
 __device__ __forceinline__ double fx_out_q(U128 q, int ef)
@@ -194,8 +214,8 @@ __device__ __forceinline__ FxQuad fx_quad(const Nb<double> &v, int ef)
                           (fx_cv<NEAR>(v.xpzm, ef) + fx_cv<NEAR>(v.xmzp, ef));
     const long long cyz = (fx_cv<NEAR>(v.ypzp, ef) + fx_cv<NEAR>(v.ymzm, ef)) -
                           (fx_cv<NEAR>(v.ypzm, ef) + fx_cv<NEAR>(v.ymzp, ef));
-    const U128 E = add128(mul_s64(a, amb), mul_s64(b, b));                                   // E / 2 >= 0
-    const U128 C = add128(add128(mul_s64(cxy, cxy), mul_s64(cxz, cxz)), mul_s64(cyz, cyz));  // >= 0
+    const U128 E = add128(mul_s64(a, amb), sqr_s64(b));                                      // E / 2 >= 0
+    const U128 C = add128(add128(sqr_s64(cxy), sqr_s64(cxz)), sqr_s64(cyz));                 // >= 0
     const U128 Q = add128(shl128(E, 4), add128(C, shl128(C, 1)));                             // 16 E/2 + 3 C
     FxQuad r;
     r.q = fx_out_q(Q, ef);

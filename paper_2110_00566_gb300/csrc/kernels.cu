@@ -98,17 +98,18 @@ k_smooth2(const T *__restrict__ Uc, const T *__restrict__ Uo, T *__restrict__ Un
 {
     // the smoother's constants, formed once per block (FP64 adds issue at a
     // small fraction of the integer rate on this GPU)
-    __shared__ T cf_s[2];
+    __shared__ T cf_s;
+    __shared__ NtK nk_s;
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-        cf_s[0] = smooth_cf<T>(sc);
-        cf_s[1] = opp->sgn75 * (T)dk.kq;
+        cf_s = smooth_cf<T>(sc);
+        if constexpr (sizeof(T) == 8) nk_s = make_ntk(*opp, dk);
     }
     __syncthreads();
     const int mp2 = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int i = blockIdx.z;
     if (2 * mp2 >= L.half || j >= L.n) return;
-    smooth_pair<T, CORR>(*opp, L, Uc, Uo, Un, Sc, Fc, cf_s[0], cf_s[1], colour, Bc, Bo, i, j, 2 * mp2, dk);
+    smooth_pair<T, CORR>(*opp, L, Uc, Uo, Un, Sc, Fc, cf_s, nk_s, colour, Bc, Bo, i, j, 2 * mp2, dk);
 }
 
 // four cells of an FP32 colour row per thread (rows whose length is a
@@ -194,6 +195,12 @@ void launch_smooth(const LevArrays<T> &L, LevArrays<T> *Lw, const OpK<T> *op, in
     if (launch_smooth4<T>(L, K, op, colour, nb, st)) {
         Lw->cur[colour] = nb;
         return;
+    }
+    if constexpr (sizeof(T) == 8) {
+        if (launch_smooth_bfp(L, K, op, colour, nb, st)) {
+            Lw->cur[colour] = nb;
+            return;
+        }
     }
     if (L.half % 2 == 0) {
         const dim3 b = block_mj(L.half / 2);
@@ -281,6 +288,12 @@ template <typename T>
 void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb, cudaStream_t st,
                        float *const *D, bool zero_u)
 {
+    // (a zero field on an eligible level runs the same kernel as any other
+    // field, so that its norms come out bit-identical to a warm start from
+    // an explicit zero field)
+    if constexpr (sizeof(T) == 8) {
+        if (launch_resid_norm_bfp(L, op, rb, st, D)) return;
+    }
     const dim3 b = block_mj(L.half);
     dim3 g = grid_mj(L.half, L.n, b, 1);
     g.z = red_z(g, 2 * L.n, rb.cap);
@@ -392,6 +405,9 @@ template <typename T>
 void launch_resid_restrict(const LevArrays<T> &Lf, LevArrays<T> &Lc, const OpK<T> *op, const RedBuf &rb,
                            cudaStream_t st)
 {
+    if constexpr (sizeof(T) == 8) {
+        if (launch_resid_restrict_bfp(Lf, Lc, op, rb, st)) return;
+    }
     if (launch_resid_restrict4<T>(Lf, Lc, op, rb, st)) return;
     const int nc = Lf.n / 2;
     const dim3 b = block_mj(nc);

@@ -42,6 +42,20 @@ void launch_smooth_shape(const LevArrays<T> &L, const OpK<T> *op, int colour, in
 // kernel
 bool launch_smooth4_shape(const LevArrays<float> &L, const OpK<float> *op, int colour, int bx, int zc,
                           cudaStream_t st);
+// FP64 nDGP half-sweep with the stencil staged once per block in shared
+// memory as block fixed point (smooth_bfp.cu), into buffer nb; false when
+// the level is not eligible (correction form, Kmouflage, half % 32 != 0 or
+// n % 8 != 0)
+bool launch_smooth_bfp(const LevArrays<double> &L, const LevK<double> &K, const OpK<double> *op, int colour, int nb,
+                       cudaStream_t st);
+// FP64 nDGP residual passes with the stencil staged in shared memory as
+// block fixed point (resid_bfp.cu): the fused residual/restriction into the
+// coarse level Lc, and the residual norm (with D set, -d as FP32); false when
+// the level is not eligible (as launch_smooth_bfp)
+bool launch_resid_restrict_bfp(const LevArrays<double> &Lf, LevArrays<double> &Lc, const OpK<double> *op,
+                               const RedBuf &rb, cudaStream_t st);
+bool launch_resid_norm_bfp(const LevArrays<double> &L, const OpK<double> *op, const RedBuf &rb, cudaStream_t st,
+                           float *const *D);
 // streaming FP32 four-cell half-sweep (shared-memory plane ring fed by bulk
 // asynchronous copies) for n = 256 and 512: variants 1 .. stream_variants()
 // (ring depth and planes per block); false when the level is not eligible

@@ -61,7 +61,7 @@ k_math_probe(const double *__restrict__ x, double *__restrict__ y, long long n, 
             // a cell whose stencil has Q = 0 and density term s = v on a level
             // of spacing h = 1: the residual kernels' N
             int cl = 0;
-            r = dgp64_N(op, dk, fma(dk.w24, v, 0.0), cl);
+            r = dgp64_N_any(op, dk, make_ntk(op, dk), 0.0, v, cl);
         }
         y[q] = r;
     }

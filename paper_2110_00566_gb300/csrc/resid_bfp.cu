@@ -1,0 +1,198 @@
+// FP64 nDGP residual passes (Sec. 3.2.1 of arXiv:2110.00566: d = L(u) - f,
+// its rms and <N>) with the stencil staged once per block in shared memory
+// as block fixed-point integers (bfp.cuh), for levels whose colour rows are a
+// multiple of 32 long:
+//   RR = true:  the fused residual and FAS restriction (R u, R d of the 8
+//               children of every coarse cell, Eq. general_pde_numerical_coarse),
+//   RR = false: the residual norm only, optionally writing -d as FP32 (the
+//               FP64 defect of the mixed-precision solve).
+// Both reduce (sum N, sum d, sum d^2, square-root clamps) over the grid in a
+// fixed order (deterministic).  Per fine cell: S6 - 6u exact in 64-bit
+// integers and Q16 exact in 128 bits, each rounded once (as fixsum.cuh), N
+// from the FP32 estimate with one FP64 Newton step (dgp64_N_nt) or the
+// rationalised FP64 form where that is not safe; d = (S6 - 6u)/h^2 - N - f
+// + cshift.
+//
+// Threads: a warp covers 16 split-index columns of two rows (2J, 2J + 1) of
+// the tile, and each thread the two cells (one of each colour) at its row and
+// split index m, which are the children of the coarse cell (J, K = m) in that
+// plane; a block walks pairs of planes (2I, 2I + 1), so the 8 children of a
+// coarse cell are the two planes of two partner lanes.
+#include <algorithm>
+
+#include "bfp.cuh"
+#include "cells.cuh"
+#include "kernels.cuh"
+
+namespace mg {
+
+template <bool RR>
+__global__ void __launch_bounds__(bfp::THREADS, 2)
+k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const double *__restrict__ S0,
+            const double *__restrict__ S1, const double *__restrict__ F0, const double *__restrict__ F1, LevScal *sc,
+            RedBuf rb, LevK<double> L, const OpK<double> *__restrict__ opp, double *__restrict__ Uc0,
+            double *__restrict__ Uc1, double *__restrict__ URc0, double *__restrict__ URc1,
+            double *__restrict__ RDc0, double *__restrict__ RDc1, float *__restrict__ D0, float *__restrict__ D1,
+            DgpK64 dk, int zc)
+{
+    __shared__ bfp::Shared t;
+    __shared__ double s_c[2];
+    __shared__ NtK s_nk;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int jt = 2 * (warp >> 1) + (lane >> 4), mt = 16 * (warp & 1) + (lane & 15);
+    const int n = L.n, half = L.half;
+    const int m0 = blockIdx.x * bfp::TM, j0 = blockIdx.y * bfp::TJ;
+    const int i0 = blockIdx.z * zc, i1 = min(n, i0 + zc);
+    if (tid == 0) {
+        s_c[0] = sc->c;
+        s_c[1] = sc->c - sc->fshift;
+        s_nk = make_ntk(*opp, dk);
+    }
+    // ring colour slots: 0 = the colour-0 array, 1 = the colour-1 array
+    bfp::Stager g(t, U0, U1, n, half, m0, j0, tid);
+    g.fill(i0);
+    const double c_old = s_c[0], cshift = s_c[1];
+    const NtK nk = s_nk;
+    const OpK<double> &op = *opp;
+    const int j = j0 + jt, m = m0 + mt;
+    const int jj = jt + 1, mm = mt + 1;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};   // sum N, sum d, sum d^2, clamps
+    double su = 0.0, sd = 0.0;              // this thread's children of the coarse cell
+    const long long rowo = (long long)j * half + m;
+    // the cells' s and f are read a plane ahead, like the staged planes
+    double s_nx[2], f_nx[2] = {0.0, 0.0};
+    {
+        const long long r0 = (long long)i0 * g.pstride + rowo;
+        s_nx[0] = __ldg(S0 + r0);
+        s_nx[1] = __ldg(S1 + r0);
+        if (F0) {
+            f_nx[0] = __ldg(F0 + r0);
+            f_nx[1] = __ldg(F1 + r0);
+        }
+    }
+    for (int i = i0, step = 0; i < i1; ++i, ++step) {
+        const bool more = i + 1 < i1;
+        const long long rowi = (long long)i * g.pstride + rowo;
+        const double sv[2] = {s_nx[0], s_nx[1]}, fv[2] = {f_nx[0], f_nx[1]};
+        if (more) {
+            g.prefetch(i + 2);
+            s_nx[0] = __ldg(S0 + rowi + g.pstride);
+            s_nx[1] = __ldg(S1 + rowi + g.pstride);
+            if (F0) {
+                f_nx[0] = __ldg(F0 + rowi + g.pstride);
+                f_nx[1] = __ldg(F1 + rowi + g.pstride);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int p = (c + i + j) & 1;
+            const double s = sv[c];
+            const double *F = c ? F1 : F0;
+            double N, d, u;
+            int cl = 0;
+            if (fx_ok(g.ef)) {
+                const bfp::Sums r = bfp::stencil(t.v[g.sm], t.v[g.s0], t.v[g.sp], c, jj, mm, p);
+                const long long U = bfp::at(t.v[g.s0], c, jj, mm);
+                u = t.raw[g.s0][c * bfp::PLANE + jj * bfp::W + mm];
+                const double q = bfp::quad(r, g.ef);
+                const double lap6 = fx_out((r.X + r.Y + r.Z) - ((U << 2) + (U << 1)), g.ef);
+                N = dgp64_N_any(op, dk, nk, q, s, cl);
+                d = fma(L.inv_h2, lap6, cshift - N);
+                if (F) d -= fv[c];
+            } else {
+                Nb<double> v;
+                gather(v, c ? U1 : U0, c ? U0 : U1, n, half, i, j, m, p);
+                u = __ldg((c ? U1 : U0) + rowi);
+                d = dgp64_resid(op, dk, nk, v, u, s, F ? F + rowi : nullptr, cshift, L.inv_h2, N, cl);
+            }
+            acc[0] += N;
+            acc[2] = fma(d, d, acc[2]);
+            if (cl) acc[3] += 1.0;
+            if (RR) {
+                sd += d;
+                su += u;
+            } else {
+                acc[1] += d;
+                if (D0) (c ? D1 : D0)[rowi] = (float)(-d);
+            }
+        }
+        if (RR && (i & 1)) {
+            // the coarse cell (I, J, K) = (i/2, j/2, m): this lane's 4 children
+            // plus the partner row's
+            sd += __shfl_xor_sync(0xffffffffu, sd, 16);
+            su += __shfl_xor_sync(0xffffffffu, su, 16);
+            if (!(lane & 16)) {
+                const int nc = n / 2, halfc = nc / 2;
+                const int I = i >> 1, J = j >> 1, K = m;
+                const int C = (I + J + K) & 1;
+                const long long cidx = ((long long)I * nc + J) * halfc + (K >> 1);
+                const double Ru = su * 0.125;
+                (C ? Uc1 : Uc0)[cidx] = Ru;
+                (C ? URc1 : URc0)[cidx] = Ru;
+                (C ? RDc1 : RDc0)[cidx] = sd * 0.125;
+                acc[1] += sd;
+            }
+            sd = 0.0;
+            su = 0.0;
+        }
+        if (!more) break;
+        g.advance(step);
+    }
+    double tot[4];
+    if (grid_sum<4>(acc, rb, tot) && tid == 0) {
+        const double cnt = (double)n * n * n;
+        const double c_new = tot[0] / cnt;
+        const double dc = c_new - c_old;
+        set_c(sc, c_new);
+        sc->dc = dc;
+        sc->eps2 = (tot[2] + 2.0 * dc * tot[1] + cnt * dc * dc) / cnt;
+        sc->sumN = tot[0];
+        sc->clamps = tot[3];
+    }
+}
+
+// planes per block: an even count (a block walks whole coarse planes) that
+// keeps the grid within the reduction buffer's capacity
+static int bfp_planes(const LevArrays<double> &L, int cap)
+{
+    const long long tiles = (long long)(L.half / bfp::TM) * (L.n / bfp::TJ);
+    int zc = 8;
+    while (zc < L.n && tiles * ((L.n + zc - 1) / zc) > cap) zc *= 2;
+    return std::min(zc, L.n);
+}
+
+static bool bfp_eligible(const LevArrays<double> &L)
+{
+    return !L.base[0] && L.model == 0 && L.half % bfp::TM == 0 && L.n % bfp::TJ == 0;
+}
+
+bool launch_resid_restrict_bfp(const LevArrays<double> &Lf, LevArrays<double> &Lc, const OpK<double> *op,
+                               const RedBuf &rb, cudaStream_t st)
+{
+    if (!bfp_eligible(Lf)) return false;
+    const int zc = bfp_planes(Lf, rb.cap);
+    const dim3 b(bfp::THREADS, 1, 1);
+    const dim3 g(Lf.half / bfp::TM, Lf.n / bfp::TJ, (Lf.n + zc - 1) / zc);
+    if ((long long)g.x * g.y * g.z > rb.cap) return false;
+    k_resid_bfp<true><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb,
+                                       make_levk<double>(Lf.n, Lf.h), op, Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1],
+                                       Lc.fbuf[0], Lc.fbuf[1], nullptr, nullptr, make_dgpk64(Lf.h), zc);
+    return true;
+}
+
+bool launch_resid_norm_bfp(const LevArrays<double> &L, const OpK<double> *op, const RedBuf &rb, cudaStream_t st,
+                           float *const *D)
+{
+    if (!bfp_eligible(L)) return false;
+    const int zc = bfp_planes(L, rb.cap);
+    const dim3 b(bfp::THREADS, 1, 1);
+    const dim3 g(L.half / bfp::TM, L.n / bfp::TJ, (L.n + zc - 1) / zc);
+    if ((long long)g.x * g.y * g.z > rb.cap) return false;
+    k_resid_bfp<false><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb,
+                                        make_levk<double>(L.n, L.h), op, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                        nullptr, D ? D[0] : nullptr, D ? D[1] : nullptr, make_dgpk64(L.h), zc);
+    return true;
+}
+
+}  // namespace mg

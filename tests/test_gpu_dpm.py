@@ -170,3 +170,43 @@ def test_checkpoint_interval_does_not_change_the_gradient(B, ctx):
         assert L == outs[0][0]
         assert rel(out, outs[0][2]) < 1e-12
         assert drc == pytest.approx(outs[0][1], rel=1e-12)
+
+
+def test_autograd_pm_with_a_loss_of_the_callers(B, ctx):
+    """The run behind torch.autograd.Function (binding.autograd_pm, backward by
+    dpm_run_vjp): a loss the library does not know -- a weighted squared
+    log-ratio of P to a target -- differentiated by loss.backward() against
+    the oracle's FP64 autograd gradient of the same loss at 16^3 (dL/dw to
+    1e-7, dL/dR_c to 1e-6), and the built-in MSE through the same Function
+    against dpm_run's own gradient."""
+    oc, gc, amp = cfgs(B, model=1, K=2)
+    n, rc = oc.ng, 1.3
+    w = inputs.white_noise(n, 741)
+    tgt = torch.from_numpy(target_for(oc, amp))
+    wts = torch.linspace(1.0, 2.0, oc.nbins, dtype=torch.float64)
+    o = B.opts(rtol=1e-12, max_cycles=60)
+    Fn = B.autograd_pm()
+    wt = torch.from_numpy(w).cuda().requires_grad_(True)
+    rt = torch.tensor(rc, dtype=torch.float64, requires_grad=True)
+    pk = Fn.apply(wt, rt, ctx, gc, amp, o)
+    L = (wts.cuda() * torch.log(pk / tgt.cuda()) ** 2).sum()
+    L.backward()
+    # the oracle: the same loss on its own P by torch autograd
+    wo = torch.tensor(w, requires_grad=True)
+    ro = torch.tensor(rc, dtype=torch.float64, requires_grad=True)
+    delta, _, _ = odpm.forward(wo, ro, amp, oc, oracle.Opts(rtol=1e-12, max_cycles=60))
+    pko, _ = odpm.power_spectrum(delta, oc.box, oc.nbins)
+    Lo = (wts * torch.log(pko / tgt) ** 2).sum()
+    Lo.backward()
+    assert float(L) == pytest.approx(float(Lo), rel=1e-9)
+    assert rel(wt.grad.cpu().numpy(), wo.grad.numpy()) < 1e-7
+    assert float(rt.grad) == pytest.approx(float(ro.grad), rel=1e-6)
+    # the built-in MSE through the Function equals dpm_run's gradient
+    wt.grad = None
+    rt.grad = None
+    pk = Fn.apply(wt, rt, ctx, gc, amp, o)
+    ((pk - tgt.cuda()) ** 2).mean().backward()
+    ref = np.empty((n, n, n))
+    _, _, drc, _ = B.dpm_run(ctx, gc, amp, w, rc, tgt.numpy(), ref, o=o)
+    assert rel(wt.grad.cpu().numpy(), ref) < 1e-12
+    assert float(rt.grad) == pytest.approx(drc, rel=1e-12)

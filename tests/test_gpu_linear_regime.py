@@ -95,7 +95,7 @@ def test_fp64_N_relative_at_every_amplitude(B, ctx, alpha):
     assert float(yc[0]) == -0.75 * alpha
 
 
-@pytest.mark.parametrize("n,h", [(16, 1.0), (32, 2.0)])
+@pytest.mark.parametrize("n,h", [(16, 1.0), (32, 2.0), (64, 1.0), (128, 4.0)])
 def test_smoother_and_residual_N_at_small_amplitude(B, ctx, n, h):
     """The FP64 smoother and fused residual/restriction at amplitude 1e-6
     (density term) and 1e-9 (field): the N part of the update and of the

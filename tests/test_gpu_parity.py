@@ -59,7 +59,7 @@ def fields(n, seed, amp):
 
 @pytest.mark.parametrize("name", list(MODELS))
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("n,h", [(16, 1.0), (24, 4.0), (8, 2.0)])
+@pytest.mark.parametrize("n,h", [(16, 1.0), (24, 4.0), (8, 2.0), (64, 2.0), (192, 1.0)])
 def test_smooth_half_sweep(B, ctx, name, prec, n, h):
     o, b, amp = ops(B, name)
     u, s, f = fields(n, 10, amp)
