@@ -69,6 +69,9 @@ def args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-forms", action="store_true")
+    p.add_argument("--forms", default="all",
+                   help="comma-separated forms to run: mixed, accuracy, rc5, batched, adjoint, adjoint_pm, "
+                        "kmouflage, cycles (default all; --no-forms runs none)")
     p.add_argument("--inner", type=int, default=0, help="FP32 cycles per FP64 defect (0: library default)")
     p.add_argument("--fp32-smoother", type=int, default=0,
                    help="FP32 half-sweep kernel: 0 autotuned, -1 gathering, k >= 1 streaming variant k")
@@ -811,13 +814,20 @@ def main():
                 "dL_dRc": drc, "fd_rel_err_Rc": abs(drc - fdr) / max(abs(fdr), 1e-300),
                 "precision": "fp64 particles and solves"}
 
+    names = set() if a.no_forms else (
+        {"mixed", "accuracy", "rc5", "batched", "adjoint", "adjoint_pm", "kmouflage", "cycles"} if a.forms == "all"
+        else set(x.strip() for x in a.forms.split(",") if x.strip()))
+
+    def want(f):
+        return f in names
+
     primary = timed(a.precision)
     second = None
-    if not a.no_forms:
+    if want("mixed"):
         second = timed("mixed" if a.precision == "fp64" else "fp64")
-    acc_form = at_accuracy(delta, a.rc) if not a.no_forms else None
+    acc_form = at_accuracy(delta, a.rc) if want("accuracy") else None
     rc5_form = None
-    if not a.no_forms and a.pm_steps > 0 and a.rc != 5.0:
+    if want("rc5") and a.pm_steps > 0 and a.rc != 5.0:
         # the run and the headline solve at H0 r_c = 5: its own z = 0 density
         pos5, pm_forms["rc5"] = pm_run(5.0)
         d5 = torch.empty_like(delta)
@@ -843,15 +853,15 @@ def main():
                               "final_eps_over_eps_ref": st5[0].eps[st5[0].n_eps - 1] / st5[0].eps_ref}
         del d5
     kmo_pos = None
-    if not a.no_forms and a.pm_steps > 0:
+    if want("kmouflage") and a.pm_steps > 0:
         kmo_pos, pm_forms["gr_512mpch"] = pm_run(0.0, model=0, box=2.0 * a.box)
     e2e_primary = None if a.no_e2e else e2e(primary)
-    batch_form = batched() if (a.batch > 0 and not a.no_forms) else None
-    adj_form = adjoint() if (a.adj_ng > 0 and not a.no_forms) else None
-    pm_adj_form = adjoint_pm() if (a.pm_adj_ng > 0 and not a.no_forms) else None
-    kmo_form = kmouflage(kmo_pos) if not a.no_forms else None
+    batch_form = batched() if (a.batch > 0 and want("batched")) else None
+    adj_form = adjoint() if (a.adj_ng > 0 and want("adjoint")) else None
+    pm_adj_form = adjoint_pm() if (a.pm_adj_ng > 0 and want("adjoint_pm")) else None
+    kmo_form = kmouflage(kmo_pos) if want("kmouflage") else None
     kmo_pos = None
-    cyc_form = cycle_types() if not a.no_forms else None
+    cyc_form = cycle_types() if want("cycles") else None
 
     if rank != 0:
         if dist:

@@ -13,9 +13,9 @@
 // the largest value of the three planes.  When the next plane raises E the
 // staged planes are shifted down to it (sign and magnitude: exactly the
 // values a direct conversion at the new scale gives); when E falls by more
-// than two binades they are converted again from their FP64 values, kept in a
-// second ring, so that the scale never exceeds the local largest value by
-// more than 2^2.  Outside the fixed-point domain (fx_ok: a value above 2^506,
+// than two binades they are read again (from L2) and converted at the new
+// scale, so that the scale never exceeds the local largest value by more
+// than 2^2.  Outside the fixed-point domain (fx_ok: a value above 2^506,
 // NaN or infinity) the caller evaluates those planes' cells in FP64.
 //
 // Use: construct, fill(i0), then per plane i: prefetch(i + 2) before the
@@ -28,20 +28,26 @@
 namespace mg {
 namespace bfp {
 
-constexpr int TM = 32;                  // split-index columns per tile
-constexpr int TJ = 8;                   // rows per tile
-constexpr int W = TM + 2;               // the tile with the k+-1 halo columns
-constexpr int H = TJ + 2;               // and the j+-1 halo rows
-constexpr int PLANE = W * H;            // values per colour and plane
-constexpr int LOAD = 2 * PLANE;         // values staged per plane (both colours)
-constexpr int THREADS = TM * TJ;
-constexpr int PER = (LOAD + THREADS - 1) / THREADS;
+constexpr int TM = 32;                  // split-index columns of the stencil kernels' tiles
+constexpr int W = TM + 2;               // with the k+-1 halo columns
+constexpr int THREADS = 256;
 
+// a tile of TMc split-index columns and TJ rows with a one-cell halo: values
+// per colour and plane, values staged per plane (both colours) and per thread
+template <int TJ, int TMc = TM>
+struct Tile {
+    static constexpr int Wc = TMc + 2;
+    static constexpr int H = TJ + 2;
+    static constexpr int PLANE = Wc * H;
+    static constexpr int LOAD = 2 * PLANE;
+    static constexpr int PER = (LOAD + THREADS - 1) / THREADS;
+};
+
+template <int TJ, int TMc = TM>
 struct Shared {
-    long long v[3][LOAD];   // slot -> [colour][row][column]
-    double raw[3][LOAD];    // the same values in FP64
-    int pmax[3];            // each slot's largest exponent field
-    int emax[2];            // block maximum of a plane being reduced (double-buffered)
+    long long v[3][Tile<TJ, TMc>::LOAD];   // slot -> [colour][row][column]
+    int pmax[3];                           // each slot's largest exponent field
+    int emax[2];                           // block maximum of a plane being reduced (double-buffered)
 };
 
 // sign-and-magnitude shift to a coarser scale: the truncation toward zero of
@@ -56,14 +62,29 @@ __device__ __forceinline__ long long down(long long v, unsigned d)
 
 __device__ __forceinline__ int ef_of(double x) { return __double2hiint(x) & 0x7FF00000; }
 
-// the value of colour slot c (0: A0, 1: A1) at tile row r, column col
-__device__ __forceinline__ long long at(const long long *slot, int c, int r, int col)
+// a constant K at the block's scale ef, for folding into a fixed-point sum;
+// ok = false where |K| exceeds the scale's largest value (or K is not
+// finite), so that the sum could overflow: the caller adds K in FP64 instead
+__device__ __forceinline__ long long fold(double K, int ef, bool &ok)
 {
-    return slot[c * PLANE + r * W + col];
+    ok = ef_of(K) <= ef;
+    return ok ? fx_in<6>(K, ef) : 0;
 }
 
+// the value of colour slot c (0: A0, 1: A1) at tile row r, column col
+template <int TJ, int TMc = TM>
+__device__ __forceinline__ long long at(const long long *slot, int c, int r, int col)
+{
+    return slot[c * Tile<TJ, TMc>::PLANE + r * Tile<TJ, TMc>::Wc + col];
+}
+
+// S: guard bits of the conversion (fixsum.cuh): 6 for the stencil sums
+// (|V| < 2^59), 3 where 64 values are summed with integer weights
+template <int TJ, int TMc = TM, int S = 6>
 struct Stager {
-    Shared &t;
+    static constexpr int PLANE = Tile<TJ, TMc>::PLANE, LOAD = Tile<TJ, TMc>::LOAD, PER = Tile<TJ, TMc>::PER;
+    static constexpr int Wc = Tile<TJ, TMc>::Wc;
+    Shared<TJ, TMc> &t;
     const double *A0, *A1;   // the colour arrays staged as colour slots 0 and 1
     int n, tid;
     long long pstride;
@@ -76,7 +97,8 @@ struct Stager {
 
     // element e = tid + q * THREADS of a plane is colour e / PLANE, tile row
     // jj, column mm: row j0 - 1 + jj and split index m0 - 1 + mm (wrapped)
-    __device__ Stager(Shared &sh, const double *a0, const double *a1, int n_, int half, int m0, int j0, int tid_)
+    __device__ Stager(Shared<TJ, TMc> &sh, const double *a0, const double *a1, int n_, int half, int m0, int j0,
+                      int tid_)
         : t(sh), A0(a0), A1(a1), n(n_), tid(tid_), pstride((long long)n_ * half), ocol(0)
     {
 #pragma unroll
@@ -85,7 +107,7 @@ struct Stager {
             const int ee = e < LOAD ? e : 0;
             const int col = ee >= PLANE;
             const int r = ee - col * PLANE;
-            const int jj = r / W, mm = r - jj * W;
+            const int jj = r / Wc, mm = r - jj * Wc;
             int j = j0 - 1 + jj, m = m0 - 1 + mm;
             j = j < 0 ? j + n : (j >= n ? j - n : j);
             m = m < 0 ? m + half : (m >= half ? m - half : m);
@@ -120,19 +142,23 @@ struct Stager {
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const int e = tid + q * THREADS;
-            if (e < LOAD) {
-                t.raw[s][e] = x[q];
-                t.v[s][e] = fx_in<6>(x[q], ef);
-            }
+            if (e < LOAD) t.v[s][e] = fx_in<S>(x[q], ef);
         }
     }
     __device__ void shift_down(int s, unsigned d)
     {
         for (int e = tid; e < LOAD; e += THREADS) t.v[s][e] = down(t.v[s][e], d);
     }
-    __device__ void reconvert(int s)
+    // plane ip read again into slot s at the current scale (x is in use for
+    // the next plane, so this thread's elements are read one at a time)
+    __device__ void reconvert(int s, int ip)
     {
-        for (int e = tid; e < LOAD; e += THREADS) t.v[s][e] = fx_in<6>(t.raw[s][e], ef);
+        const long long base = (long long)wrap(ip) * pstride;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * THREADS;
+            if (e < LOAD) t.v[s][e] = fx_in<S>(__ldg(((ocol >> q) & 1 ? A1 : A0) + base + goff[q]), ef);
+        }
     }
     // planes i0 - 1, i0, i0 + 1 into slots 0, 1, 2; each plane's maximum is
     // reduced on its own (reduction slot q & 1; the other slot, read before
@@ -175,9 +201,10 @@ struct Stager {
         s0 = 1;
         sp = 2;
     }
-    // stage the prefetched plane into the slot of the oldest plane, at the
-    // scale of the new triple, and rotate the slots (step counts from 0)
-    __device__ void advance(int step)
+    // after the update of plane i: stage the prefetched plane i + 2 into the
+    // slot of plane i - 1, at the scale of planes i, i + 1, i + 2, and rotate
+    // the slots (step counts from 0)
+    __device__ void advance(int step, int i)
     {
         block_max(step & 1, xmax());
         __syncthreads();
@@ -194,8 +221,8 @@ struct Stager {
         } else if (Et < E - (2 << 20)) {
             E = Et;
             ef = fx_zero_scale(E);
-            reconvert(s0);
-            reconvert(sp);
+            reconvert(s0, i);
+            reconvert(sp, i + 1);
         }
         store(sm);
         if (tid == 0) {
@@ -217,29 +244,34 @@ struct Stager {
 struct Sums {
     long long X, Y, Z, cxy, cxz, cyz;
 };
+template <int TJ>
 __device__ __forceinline__ Sums stencil(const long long *Sm, const long long *S0, const long long *Sp, int c, int jj,
                                         int mm, int p)
 {
     const int o = 1 - c;
     Sums r;
-    r.X = at(Sp, o, jj, mm) + at(Sm, o, jj, mm);
-    r.Y = at(S0, o, jj + 1, mm) + at(S0, o, jj - 1, mm);
-    r.Z = at(S0, o, jj, mm + p) + at(S0, o, jj, mm + p - 1);
-    r.cxy = (at(Sp, c, jj + 1, mm) + at(Sm, c, jj - 1, mm)) - (at(Sp, c, jj - 1, mm) + at(Sm, c, jj + 1, mm));
-    r.cxz = (at(Sp, c, jj, mm + p) + at(Sm, c, jj, mm + p - 1)) - (at(Sp, c, jj, mm + p - 1) + at(Sm, c, jj, mm + p));
-    r.cyz = (at(S0, c, jj + 1, mm + p) + at(S0, c, jj - 1, mm + p - 1)) -
-            (at(S0, c, jj + 1, mm + p - 1) + at(S0, c, jj - 1, mm + p));
+    r.X = at<TJ>(Sp, o, jj, mm) + at<TJ>(Sm, o, jj, mm);
+    r.Y = at<TJ>(S0, o, jj + 1, mm) + at<TJ>(S0, o, jj - 1, mm);
+    r.Z = at<TJ>(S0, o, jj, mm + p) + at<TJ>(S0, o, jj, mm + p - 1);
+    r.cxy = (at<TJ>(Sp, c, jj + 1, mm) + at<TJ>(Sm, c, jj - 1, mm)) -
+            (at<TJ>(Sp, c, jj - 1, mm) + at<TJ>(Sm, c, jj + 1, mm));
+    r.cxz = (at<TJ>(Sp, c, jj, mm + p) + at<TJ>(Sm, c, jj, mm + p - 1)) -
+            (at<TJ>(Sp, c, jj, mm + p - 1) + at<TJ>(Sm, c, jj, mm + p));
+    r.cyz = (at<TJ>(S0, c, jj + 1, mm + p) + at<TJ>(S0, c, jj - 1, mm + p - 1)) -
+            (at<TJ>(S0, c, jj + 1, mm + p - 1) + at<TJ>(S0, c, jj - 1, mm + p));
     return r;
 }
 
-// Q16 = 16 (a (a - b) + b^2) + 3 (C_xy^2 + C_xz^2 + C_yz^2), exact in 128 bits
-// (a = X - Y, b = X - Z), rounded once to binary64 at the scale ef
+// Q16 = 16 (a (a - b) + b^2) + 3 (C_xy^2 + C_xz^2 + C_yz^2) with a = X - Y,
+// b = X - Z, as 8 (a^2 + b^2 + (a - b)^2) + 3 (C_xy^2 + C_xz^2 + C_yz^2)
+// (16 (a^2 - a b + b^2) = 8 (2 a^2 + 2 b^2 - 2 a b)): six unsigned squares,
+// exact in 128 bits, rounded once to binary64 at the scale ef
 __device__ __forceinline__ double quad(const Sums &r, int ef)
 {
     const long long a = r.X - r.Y, b = r.X - r.Z, amb = r.Z - r.Y;
-    const U128 Eh = add128(mul_s64(a, amb), sqr_s64(b));
+    const U128 A = add128(add128(sqr_s64(a), sqr_s64(b)), sqr_s64(amb));
     const U128 C = add128(add128(sqr_s64(r.cxy), sqr_s64(r.cxz)), sqr_s64(r.cyz));
-    return fx_out_q(add128(shl128(Eh, 4), add128(C, shl128(C, 1))), ef);
+    return fx_out_q(add128(shl128(A, 3), add128(C, shl128(C, 1))), ef);
 }
 
 }  // namespace bfp

@@ -543,6 +543,9 @@ void launch_prolong(const LevArrays<T> &Lf, const LevArrays<T> &Lc, cudaStream_t
     const long long nc = Lc.ncol;
     const int eb = (int)std::min<long long>((nc + 255) / 256, 152LL * 16);
     k_coarse_e<T><<<eb, 256, 0, st>>>(Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1], nc);
+    if constexpr (sizeof(T) == 8) {
+        if (launch_prolong_bfp(Lf, Lc, st)) return;
+    }
     const dim3 b = block_mj(Lf.half);
     const dim3 g = grid_mj(Lf.half, Lf.n, b, 2 * Lf.n);
     k_prolong_e<T><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lc.ur[0], Lc.ur[1], Lf.n);

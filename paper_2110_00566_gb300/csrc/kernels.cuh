@@ -56,6 +56,11 @@ bool launch_resid_restrict_bfp(const LevArrays<double> &Lf, LevArrays<double> &L
                                const RedBuf &rb, cudaStream_t st);
 bool launch_resid_norm_bfp(const LevArrays<double> &L, const OpK<double> *op, const RedBuf &rb, cudaStream_t st,
                            float *const *D);
+// FP64 prolongation of the coarse correction held in Lc.ur (formed by the
+// coarse-correction pass) with the coarse planes staged in shared memory as
+// block fixed point (prolong_bfp.cu); false when the fine level is not
+// eligible (n < 128, rows not a multiple of 64 long)
+bool launch_prolong_bfp(const LevArrays<double> &Lf, const LevArrays<double> &Lc, cudaStream_t st);
 // streaming FP32 four-cell half-sweep (shared-memory plane ring fed by bulk
 // asynchronous copies) for n = 256 and 512: variants 1 .. stream_variants()
 // (ring depth and planes per block); false when the level is not eligible

@@ -26,6 +26,17 @@
 
 namespace mg {
 
+namespace {
+constexpr int RR_TJ = 8;   // tile rows: a warp covers 16 columns of two rows
+
+// d where the pass's shift does not fit the block's scale (rare), out of
+// line so that the compiler does not predicate it into every cell
+__device__ __noinline__ double resid_shift_fp64(double inv_h2, long long lap6, int ef, double cshift, double N)
+{
+    return fma(inv_h2, fx_out(lap6, ef), cshift - N);
+}
+}
+
 template <bool RR>
 __global__ void __launch_bounds__(bfp::THREADS, 2)
 k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const double *__restrict__ S0,
@@ -35,14 +46,14 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
             double *__restrict__ RDc0, double *__restrict__ RDc1, float *__restrict__ D0, float *__restrict__ D1,
             DgpK64 dk, int zc)
 {
-    __shared__ bfp::Shared t;
+    __shared__ bfp::Shared<RR_TJ> t;
     __shared__ double s_c[2];
     __shared__ NtK s_nk;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int jt = 2 * (warp >> 1) + (lane >> 4), mt = 16 * (warp & 1) + (lane & 15);
     const int n = L.n, half = L.half;
-    const int m0 = blockIdx.x * bfp::TM, j0 = blockIdx.y * bfp::TJ;
+    const int m0 = blockIdx.x * bfp::TM, j0 = blockIdx.y * RR_TJ;
     const int i0 = blockIdx.z * zc, i1 = min(n, i0 + zc);
     if (tid == 0) {
         s_c[0] = sc->c;
@@ -50,7 +61,7 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
         s_nk = make_ntk(*opp, dk);
     }
     // ring colour slots: 0 = the colour-0 array, 1 = the colour-1 array
-    bfp::Stager g(t, U0, U1, n, half, m0, j0, tid);
+    bfp::Stager<RR_TJ> g(t, U0, U1, n, half, m0, j0, tid);
     g.fill(i0);
     const double c_old = s_c[0], cshift = s_c[1];
     const NtK nk = s_nk;
@@ -58,7 +69,13 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
     const int j = j0 + jt, m = m0 + mt;
     const int jj = jt + 1, mm = mt + 1;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};   // sum N, sum d, sum d^2, clamps
+    int nclamp = 0;                         // (counted in an integer: no FP64 add per cell)
     double su = 0.0, sd = 0.0;              // this thread's children of the coarse cell
+    // the pass's constant shift h^2 cshift folded into the fixed-point
+    // S6 - 6u (one FP64 add less per cell), where it fits the scale
+    const double kc = cshift * L.h2;
+    bool kok;
+    long long kv = bfp::fold(kc, g.ef, kok);
     const long long rowo = (long long)j * half + m;
     // the cells' s and f are read a plane ahead, like the staged planes
     double s_nx[2], f_nx[2] = {0.0, 0.0};
@@ -84,39 +101,45 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
                 f_nx[1] = __ldg(F1 + rowi + g.pstride);
             }
         }
+        const bool fx = fx_ok(g.ef);
+        long long Usum = 0;   // the two centre values at this plane's scale (R u)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int p = (c + i + j) & 1;
             const double s = sv[c];
             const double *F = c ? F1 : F0;
-            double N, d, u;
+            double N, d;
             int cl = 0;
-            if (fx_ok(g.ef)) {
-                const bfp::Sums r = bfp::stencil(t.v[g.sm], t.v[g.s0], t.v[g.sp], c, jj, mm, p);
-                const long long U = bfp::at(t.v[g.s0], c, jj, mm);
-                u = t.raw[g.s0][c * bfp::PLANE + jj * bfp::W + mm];
+            if (fx) {
+                const bfp::Sums r = bfp::stencil<RR_TJ>(t.v[g.sm], t.v[g.s0], t.v[g.sp], c, jj, mm, p);
+                const long long U = bfp::at<RR_TJ>(t.v[g.s0], c, jj, mm);
+                Usum += U;
                 const double q = bfp::quad(r, g.ef);
-                const double lap6 = fx_out((r.X + r.Y + r.Z) - ((U << 2) + (U << 1)), g.ef);
+                const long long lap6 = (r.X + r.Y + r.Z) - ((U << 2) + (U << 1));   // |.| < 12 * 2^59
                 N = dgp64_N_any(op, dk, nk, q, s, cl);
-                d = fma(L.inv_h2, lap6, cshift - N);
+                if (kok)
+                    d = fma(L.inv_h2, fx_out(lap6 + kv, g.ef), -N);
+                else
+                    d = resid_shift_fp64(L.inv_h2, lap6, g.ef, cshift, N);
                 if (F) d -= fv[c];
             } else {
                 Nb<double> v;
                 gather(v, c ? U1 : U0, c ? U0 : U1, n, half, i, j, m, p);
-                u = __ldg((c ? U1 : U0) + rowi);
+                const double u = __ldg((c ? U1 : U0) + rowi);
+                if (RR) su += u;
                 d = dgp64_resid(op, dk, nk, v, u, s, F ? F + rowi : nullptr, cshift, L.inv_h2, N, cl);
             }
             acc[0] += N;
             acc[2] = fma(d, d, acc[2]);
-            if (cl) acc[3] += 1.0;
+            nclamp += cl;
             if (RR) {
                 sd += d;
-                su += u;
             } else {
                 acc[1] += d;
                 if (D0) (c ? D1 : D0)[rowi] = (float)(-d);
             }
         }
+        if (RR && fx) su += fx_out(Usum, g.ef);
         if (RR && (i & 1)) {
             // the coarse cell (I, J, K) = (i/2, j/2, m): this lane's 4 children
             // plus the partner row's
@@ -137,8 +160,10 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
             su = 0.0;
         }
         if (!more) break;
-        g.advance(step);
+        g.advance(step, i);
+        kv = bfp::fold(kc, g.ef, kok);
     }
+    acc[3] = (double)nclamp;
     double tot[4];
     if (grid_sum<4>(acc, rb, tot) && tid == 0) {
         const double cnt = (double)n * n * n;
@@ -156,15 +181,15 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
 // keeps the grid within the reduction buffer's capacity
 static int bfp_planes(const LevArrays<double> &L, int cap)
 {
-    const long long tiles = (long long)(L.half / bfp::TM) * (L.n / bfp::TJ);
-    int zc = 8;
+    const long long tiles = (long long)(L.half / bfp::TM) * (L.n / RR_TJ);
+    int zc = 2;
     while (zc < L.n && tiles * ((L.n + zc - 1) / zc) > cap) zc *= 2;
     return std::min(zc, L.n);
 }
 
 static bool bfp_eligible(const LevArrays<double> &L)
 {
-    return !L.base[0] && L.model == 0 && L.half % bfp::TM == 0 && L.n % bfp::TJ == 0;
+    return !L.base[0] && L.model == 0 && L.n >= 128 && L.half % bfp::TM == 0 && L.n % RR_TJ == 0;
 }
 
 bool launch_resid_restrict_bfp(const LevArrays<double> &Lf, LevArrays<double> &Lc, const OpK<double> *op,
@@ -173,7 +198,7 @@ bool launch_resid_restrict_bfp(const LevArrays<double> &Lf, LevArrays<double> &L
     if (!bfp_eligible(Lf)) return false;
     const int zc = bfp_planes(Lf, rb.cap);
     const dim3 b(bfp::THREADS, 1, 1);
-    const dim3 g(Lf.half / bfp::TM, Lf.n / bfp::TJ, (Lf.n + zc - 1) / zc);
+    const dim3 g(Lf.half / bfp::TM, Lf.n / RR_TJ, (Lf.n + zc - 1) / zc);
     if ((long long)g.x * g.y * g.z > rb.cap) return false;
     k_resid_bfp<true><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb,
                                        make_levk<double>(Lf.n, Lf.h), op, Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1],
@@ -187,7 +212,7 @@ bool launch_resid_norm_bfp(const LevArrays<double> &L, const OpK<double> *op, co
     if (!bfp_eligible(L)) return false;
     const int zc = bfp_planes(L, rb.cap);
     const dim3 b(bfp::THREADS, 1, 1);
-    const dim3 g(L.half / bfp::TM, L.n / bfp::TJ, (L.n + zc - 1) / zc);
+    const dim3 g(L.half / bfp::TM, L.n / RR_TJ, (L.n + zc - 1) / zc);
     if ((long long)g.x * g.y * g.z > rb.cap) return false;
     k_resid_bfp<false><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb,
                                         make_levk<double>(L.n, L.h), op, nullptr, nullptr, nullptr, nullptr, nullptr,

@@ -15,74 +15,121 @@
 
 namespace mg {
 
+namespace {
+constexpr int SM_TJ = 16;   // tile rows: each thread updates rows ty and ty + 8
+
+// the update where the level's constant is not folded into S6 / 6 (a FAS
+// source, or a constant beyond the block's scale), out of line so that the
+// compiler does not predicate it into every cell
+__device__ __noinline__ double smooth_unfolded(const OpK<double> &op, const DgpK64 &dk, const NtK &nk, double q,
+                                               double s, long long s6, int ef, double fcf)
+{
+    int cl = 0;
+    return dgp64_finish(op, dk, nk, q, s, fx_out(s6, ef), fcf, cl);
+}
+}
+
+// HASF: the level has a FAS source f (every level but the finest)
+template <bool HASF>
 __global__ void __launch_bounds__(bfp::THREADS, 2)
 k_smooth_bfp(const double *__restrict__ Uc, const double *__restrict__ Uo, double *__restrict__ Un,
              const double *__restrict__ Sc, const double *__restrict__ Fc, const LevScal *__restrict__ sc,
              LevK<double> L, const OpK<double> *__restrict__ opp, int colour, DgpK64 dk, int zc)
 {
-    __shared__ bfp::Shared t;
+    __shared__ bfp::Shared<SM_TJ> t;
     __shared__ double s_cf;
     __shared__ NtK s_nk;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * bfp::TM + tx;
     const int n = L.n, half = L.half;
-    const int m0 = blockIdx.x * bfp::TM, j0 = blockIdx.y * bfp::TJ;
+    const int m0 = blockIdx.x * bfp::TM, j0 = blockIdx.y * SM_TJ;
     const int i0 = blockIdx.z * zc, i1 = min(n, i0 + zc);
     if (tid == 0) {
         s_cf = smooth_cf<double>(sc);
         s_nk = make_ntk(*opp, dk);
     }
     // ring colour slot 0: the updated colour's array, 1: the other's
-    bfp::Stager g(t, Uc, Uo, n, half, m0, j0, tid);
+    bfp::Stager<SM_TJ> g(t, Uc, Uo, n, half, m0, j0, tid);
     g.fill(i0);
     const double cf = s_cf;
     const NtK nk = s_nk;
     const OpK<double> &op = *opp;
-    const int j = j0 + ty, m = m0 + tx;
-    const int jj = ty + 1, mm = tx + 1;
-    const long long rowo = (long long)j * half + m;
-    // the cell's s and f are read a plane ahead, like the staged planes
-    double s_nx = __ldg(Sc + (long long)i0 * g.pstride + rowo);
-    double f_nx = Fc ? __ldg(Fc + (long long)i0 * g.pstride + rowo) : 0.0;
+    // where the level has no FAS source, the update's constant -h^2 cf / 6 is
+    // folded into the fixed-point S6 / 6 (one FP64 add less per cell)
+    const double kc = dk.mh6 * cf;
+    bool kok;
+    long long kv = bfp::fold(kc, g.ef, kok);
+    bool fold = !HASF && kok;
+    const int m = m0 + tx, mm = tx + 1;
+    const long long rowo = (long long)(j0 + ty) * half + m, rows8 = 8LL * half;
+    // each cell's s and f are read a plane ahead, like the staged planes
+    double s_nx[2], f_nx[2] = {0.0, 0.0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        s_nx[h] = __ldg(Sc + (long long)i0 * g.pstride + rowo + h * rows8);
+        if (HASF) f_nx[h] = __ldg(Fc + (long long)i0 * g.pstride + rowo + h * rows8);
+    }
     for (int i = i0, step = 0; i < i1; ++i, ++step) {
         const bool more = i + 1 < i1;
-        const long long idx = (long long)i * g.pstride + rowo;
-        const double s = s_nx, fcf = Fc ? cf + f_nx : cf;
+        const long long base = (long long)i * g.pstride + rowo;
+        const double sv[2] = {s_nx[0], s_nx[1]}, fv[2] = {f_nx[0], f_nx[1]};
         if (more) {
             g.prefetch(i + 2);   // the next plane, in flight during the update
-            s_nx = __ldg(Sc + idx + g.pstride);
-            if (Fc) f_nx = __ldg(Fc + idx + g.pstride);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                s_nx[h] = __ldg(Sc + base + g.pstride + h * rows8);
+                if (HASF) f_nx[h] = __ldg(Fc + base + g.pstride + h * rows8);
+            }
         }
-        const int p = (colour + i + j) & 1;
-        double out;
-        if (fx_ok(g.ef)) {
-            const bfp::Sums r = bfp::stencil(t.v[g.sm], t.v[g.s0], t.v[g.sp], 0, jj, mm, p);
-            const double q = bfp::quad(r, g.ef);
-            const double s6d = fx_out(fx_div6(r.X + r.Y + r.Z), g.ef);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + ty + 8 * h, jj = ty + 8 * h + 1;
+            const int p = (colour + i + j) & 1;
+            const double fcf = HASF ? cf + fv[h] : cf;
+            double out;
             int cl = 0;
-            out = dgp64_finish(op, dk, nk, q, s, s6d, fcf, cl);
-        } else {
-            Nb<double> v;
-            gather(v, Uc, Uo, n, half, i, j, m, p);
-            int cl = 0;
-            out = dgp64_update(op, dk, nk, v, s, fcf, cl);
+            if (fx_ok(g.ef)) {
+                const bfp::Sums r = bfp::stencil<SM_TJ>(t.v[g.sm], t.v[g.s0], t.v[g.sp], 0, jj, mm, p);
+                const double q = bfp::quad(r, g.ef);
+                const long long s6 = fx_div6(r.X + r.Y + r.Z);
+                if (HASF)
+                    out = dgp64_finish(op, dk, nk, q, sv[h], fx_out(s6, g.ef), fcf, cl);
+                else if (fold)
+                    out = fma(dk.mh6, dgp64_N_any(op, dk, nk, q, sv[h], cl), fx_out(s6 + kv, g.ef));
+                else
+                    out = smooth_unfolded(op, dk, nk, q, sv[h], s6, g.ef, fcf);
+            } else {
+                Nb<double> v;
+                gather(v, Uc, Uo, n, half, i, j, m, p);
+                out = dgp64_update(op, dk, nk, v, sv[h], fcf, cl);
+            }
+            Un[base + h * rows8] = out;
         }
-        Un[idx] = out;
         if (!more) break;
-        g.advance(step);   // plane i + 2 into the slot of plane i - 1
+        g.advance(step, i);   // plane i + 2 into the slot of plane i - 1
+        kv = bfp::fold(kc, g.ef, kok);
+        fold = !HASF && kok;
     }
 }
 
-// the block-fixed-point half-sweep for levels with half % 32 == 0 and
-// n % 8 == 0 (n >= 64); false otherwise
+// the block-fixed-point half-sweep for levels of 128^3 and more with
+// half % 32 == 0 and n % 16 == 0; false otherwise (coarser levels have too
+// few tiles to fill the GPU with marching blocks); planes per block: 16,
+// fewer where that leaves under ~4 blocks per SM
 bool launch_smooth_bfp(const LevArrays<double> &L, const LevK<double> &K, const OpK<double> *op, int colour, int nb,
                        cudaStream_t st)
 {
-    if (L.base[0] || L.model != 0 || L.half % bfp::TM != 0 || L.n % bfp::TJ != 0) return false;
-    const int zc = L.n >= 256 ? 16 : 8;
-    const dim3 b(bfp::TM, bfp::TJ, 1);
-    const dim3 g(L.half / bfp::TM, L.n / bfp::TJ, (L.n + zc - 1) / zc);
-    k_smooth_bfp<<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], L.f[colour], L.sc, K,
-                                  op, colour, make_dgpk64(L.h), zc);
+    if (L.base[0] || L.model != 0 || L.n < 128 || L.half % bfp::TM != 0 || L.n % SM_TJ != 0) return false;
+    const long long tiles = (long long)(L.half / bfp::TM) * (L.n / SM_TJ);
+    int zc = 16;
+    while (zc > 2 && tiles * ((L.n + zc - 1) / zc) < 600) zc /= 2;
+    const dim3 b(bfp::TM, bfp::THREADS / bfp::TM, 1);
+    const dim3 g(L.half / bfp::TM, L.n / SM_TJ, (L.n + zc - 1) / zc);
+    if (L.f[colour])
+        k_smooth_bfp<true><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], L.f[colour],
+                                            L.sc, K, op, colour, make_dgpk64(L.h), zc);
+    else
+        k_smooth_bfp<false><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], nullptr,
+                                             L.sc, K, op, colour, make_dgpk64(L.h), zc);
     return true;
 }
 

@@ -54,8 +54,9 @@ def test_fp64_smoother_branches(B, ctx, lam, spread, n, h):
 
 
 @pytest.mark.parametrize("lam,spread", [(1.0, False), (1e150, False), (1e-140, False), (1.0, True)])
-def test_fp64_residual_branches(B, ctx, lam, spread):
-    n, h = 16, 2.0
+@pytest.mark.parametrize("n", [16, 128])
+def test_fp64_residual_branches(B, ctx, lam, spread, n):
+    h = 2.0
     o = oracle.OrcOp(0, ALPHA * lam, 0, 0.0, 0.0)
     b = B.op_params(0, ALPHA * lam, 2, 0.0, 0.0)
     u, s, f = case(n, 41, lam, spread)

@@ -73,7 +73,7 @@ def test_smooth_half_sweep(B, ctx, name, prec, n, h):
 
 @pytest.mark.parametrize("name", list(MODELS))
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("n,h", [(16, 1.0), (24, 2.0), (64, 1.0)])
+@pytest.mark.parametrize("n,h", [(16, 1.0), (24, 2.0), (64, 1.0), (128, 2.0)])
 def test_residual_restriction(B, ctx, name, prec, n, h):
     o, b, amp = ops(B, name)
     u, s, f = fields(n, 20, amp)
