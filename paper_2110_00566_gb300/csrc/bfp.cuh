@@ -62,13 +62,18 @@ __device__ __forceinline__ long long down(long long v, unsigned d)
 
 __device__ __forceinline__ int ef_of(double x) { return __double2hiint(x) & 0x7FF00000; }
 
-// a constant K at the block's scale ef, for folding into a fixed-point sum;
-// ok = false where |K| exceeds the scale's largest value (or K is not
-// finite), so that the sum could overflow: the caller adds K in FP64 instead
+// a constant K at the block's scale ef, for folding into a fixed-point sum
+// whose terms stay below 1.5 2^62 (S6, S6 - 6u): exact to the scale for |K|
+// up to four times the scale's largest value (|V| < 2^61, so the sum stays
+// below 2^63); ok = false beyond that (or for K not finite): the caller adds
+// K in FP64 instead
 __device__ __forceinline__ long long fold(double K, int ef, bool &ok)
 {
-    ok = ef_of(K) <= ef;
-    return ok ? fx_in<6>(K, ef) : 0;
+    const int d = ef_of(K) - ef;   // in place
+    ok = d <= (2 << 20);
+    if (!ok) return 0;
+    if (d <= 0) return fx_in<6>(K, ef);
+    return fx_in<6>(K, ef + d) << (d >> 20);
 }
 
 // the value of colour slot c (0: A0, 1: A1) at tile row r, column col

@@ -19,6 +19,7 @@
 // plane; a block walks pairs of planes (2I, 2I + 1), so the 8 children of a
 // coarse cell are the two planes of two partner lanes.
 #include <algorithm>
+#include <type_traits>
 
 #include "bfp.cuh"
 #include "cells.cuh"
@@ -29,15 +30,10 @@ namespace mg {
 namespace {
 constexpr int RR_TJ = 8;   // tile rows: a warp covers 16 columns of two rows
 
-// d where the pass's shift does not fit the block's scale (rare), out of
-// line so that the compiler does not predicate it into every cell
-__device__ __noinline__ double resid_shift_fp64(double inv_h2, long long lap6, int ef, double cshift, double N)
-{
-    return fma(inv_h2, fx_out(lap6, ef), cshift - N);
-}
 }
 
-template <bool RR>
+// HASF: the level has a FAS source f (every level but the finest)
+template <bool RR, bool HASF>
 __global__ void __launch_bounds__(bfp::THREADS, 2)
 k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const double *__restrict__ S0,
             const double *__restrict__ S1, const double *__restrict__ F0, const double *__restrict__ F1, LevScal *sc,
@@ -83,7 +79,7 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
         const long long r0 = (long long)i0 * g.pstride + rowo;
         s_nx[0] = __ldg(S0 + r0);
         s_nx[1] = __ldg(S1 + r0);
-        if (F0) {
+        if (HASF) {
             f_nx[0] = __ldg(F0 + r0);
             f_nx[1] = __ldg(F1 + r0);
         }
@@ -96,13 +92,17 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
             g.prefetch(i + 2);
             s_nx[0] = __ldg(S0 + rowi + g.pstride);
             s_nx[1] = __ldg(S1 + rowi + g.pstride);
-            if (F0) {
+            if (HASF) {
                 f_nx[0] = __ldg(F0 + rowi + g.pstride);
                 f_nx[1] = __ldg(F1 + rowi + g.pstride);
             }
         }
         const bool fx = fx_ok(g.ef);
         long long Usum = 0;   // the two centre values at this plane's scale (R u)
+        // the plane's two cells, with the shift folded (FOLD) or added in FP64:
+        // a uniform branch per plane around two straight-line copies
+        auto cells = [&](auto fold_tag) {
+        constexpr bool FOLD = decltype(fold_tag)::value;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int p = (c + i + j) & 1;
@@ -117,17 +117,17 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
                 const double q = bfp::quad(r, g.ef);
                 const long long lap6 = (r.X + r.Y + r.Z) - ((U << 2) + (U << 1));   // |.| < 12 * 2^59
                 N = dgp64_N_any(op, dk, nk, q, s, cl);
-                if (kok)
+                if (FOLD)
                     d = fma(L.inv_h2, fx_out(lap6 + kv, g.ef), -N);
                 else
-                    d = resid_shift_fp64(L.inv_h2, lap6, g.ef, cshift, N);
-                if (F) d -= fv[c];
+                    d = fma(L.inv_h2, fx_out(lap6, g.ef), cshift - N);
+                if (HASF) d -= fv[c];
             } else {
                 Nb<double> v;
                 gather(v, c ? U1 : U0, c ? U0 : U1, n, half, i, j, m, p);
                 const double u = __ldg((c ? U1 : U0) + rowi);
                 if (RR) su += u;
-                d = dgp64_resid(op, dk, nk, v, u, s, F ? F + rowi : nullptr, cshift, L.inv_h2, N, cl);
+                d = dgp64_resid(op, dk, nk, v, u, s, HASF ? F + rowi : nullptr, cshift, L.inv_h2, N, cl);
             }
             acc[0] += N;
             acc[2] = fma(d, d, acc[2]);
@@ -139,6 +139,11 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
                 if (D0) (c ? D1 : D0)[rowi] = (float)(-d);
             }
         }
+        };
+        if (fx && kok)
+            cells(std::true_type{});
+        else
+            cells(std::false_type{});
         if (RR && fx) su += fx_out(Usum, g.ef);
         if (RR && (i & 1)) {
             // the coarse cell (I, J, K) = (i/2, j/2, m): this lane's 4 children
@@ -200,9 +205,16 @@ bool launch_resid_restrict_bfp(const LevArrays<double> &Lf, LevArrays<double> &L
     const dim3 b(bfp::THREADS, 1, 1);
     const dim3 g(Lf.half / bfp::TM, Lf.n / RR_TJ, (Lf.n + zc - 1) / zc);
     if ((long long)g.x * g.y * g.z > rb.cap) return false;
-    k_resid_bfp<true><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb,
-                                       make_levk<double>(Lf.n, Lf.h), op, Lc.U(0), Lc.U(1), Lc.ur[0], Lc.ur[1],
-                                       Lc.fbuf[0], Lc.fbuf[1], nullptr, nullptr, make_dgpk64(Lf.h), zc);
+#define MG_RRB(HASF)                                                                                         \
+    k_resid_bfp<true, HASF><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb,   \
+                                             make_levk<double>(Lf.n, Lf.h), op, Lc.U(0), Lc.U(1), Lc.ur[0],      \
+                                             Lc.ur[1], Lc.fbuf[0], Lc.fbuf[1], nullptr, nullptr,                \
+                                             make_dgpk64(Lf.h), zc)
+    if (Lf.f[0])
+        MG_RRB(true);
+    else
+        MG_RRB(false);
+#undef MG_RRB
     return true;
 }
 
@@ -214,9 +226,16 @@ bool launch_resid_norm_bfp(const LevArrays<double> &L, const OpK<double> *op, co
     const dim3 b(bfp::THREADS, 1, 1);
     const dim3 g(L.half / bfp::TM, L.n / RR_TJ, (L.n + zc - 1) / zc);
     if ((long long)g.x * g.y * g.z > rb.cap) return false;
-    k_resid_bfp<false><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb,
-                                        make_levk<double>(L.n, L.h), op, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                        nullptr, D ? D[0] : nullptr, D ? D[1] : nullptr, make_dgpk64(L.h), zc);
+#define MG_RNB(HASF)                                                                                          \
+    k_resid_bfp<false, HASF><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb,           \
+                                              make_levk<double>(L.n, L.h), op, nullptr, nullptr, nullptr, nullptr, \
+                                              nullptr, nullptr, D ? D[0] : nullptr, D ? D[1] : nullptr,           \
+                                              make_dgpk64(L.h), zc)
+    if (L.f[0])
+        MG_RNB(true);
+    else
+        MG_RNB(false);
+#undef MG_RNB
     return true;
 }
 
