@@ -44,13 +44,14 @@ HBM_PEAK_FALLBACK = 6800.0
 # sqrt (1), N (2), the face sum (2), N + f - c (2), the update (3) = 41
 FLOPS_PER_CELL_FP64 = 41
 # Thread instructions per updated cell of the FP64 nDGP half-sweep
-# (k_smooth2<double>, steady state: stencil sums and the quadratic form on
-# the integer pipes), from ncu's sm__inst_executed_pipe_{fp64,alu,fma} and
-# sm__inst_executed counters at 256^3 (profiles/k_smooth2_fp64_ndgp_256.md),
-# and what each pipe issues per SM per clock: ALU and the FMA pipe's integer
-# half 4 sub-partitions x 16 lanes, all instructions 4 x 32; the FP64 rate
-# comes from the probe at run time
-FP64_MIX = {"fp64": 9.0, "alu": 425.0, "fma": 189.5, "issue": 714.0}
+# (k_smooth_bfp, the finest level: stencil staged in shared memory as block
+# fixed point, sums and quadratic form on the integer pipes), from ncu's
+# sm__inst_executed_pipe_{fp64,alu,fmaheavy} and sm__inst_executed counters
+# at 256^3 (profiles/k_smooth_bfp_fp64_ndgp_256.md), and what each pipe
+# issues per SM per clock: ALU and the FMA pipe's integer half 4
+# sub-partitions x 16 lanes, all instructions 4 x 32; the FP64 rate comes
+# from the probe at run time
+FP64_MIX = {"fp64": 5.0, "alu": 260.0, "fma": 154.0, "issue": 540.0}
 PIPE_RATE = {"alu": 64.0, "fma": 64.0, "issue": 128.0}
 
 
@@ -434,10 +435,10 @@ def main():
                 "d2h_bytes_per_step": 8 * ng ** 3}
 
     # DRAM bytes (read + write) per launch of the dominant kernels from ncu,
-    # with the mesh they were measured on (profiles/k_smooth2_fp64_ndgp_256.md
+    # with the mesh they were measured on (profiles/k_smooth_bfp_fp64_ndgp_256.md
     # and profiles/k_smooth4_fp32corr_ndgp_512.md, both at 512^3), scaled by
     # the cell count to this mesh
-    TRAFFIC = {"fp64": (1616.1e6 + 524.6e6, 512), "mixed": (1673.9e6 + 255.5e6, 512)}
+    TRAFFIC = {"fp64": (1616.4e6 + 611.4e6, 512), "mixed": (1670.8e6 + 255.4e6, 512)}
 
     def roofline(r, precision, fp64_tf):
         """Roofline of the finest half-sweep, anchored to the HBM peak (the
@@ -467,7 +468,7 @@ def main():
             bind = max(cyc, key=cyc.get)
             t_sol = cells / nsm * cyc[bind] / (mhz * 1e6)
             return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                    "traffic": traffic, "traffic_source": tsrc, "kernel": "k_smooth2<double> finest half-sweep",
+                    "traffic": traffic, "traffic_source": tsrc, "kernel": "k_smooth_bfp finest half-sweep",
                     "peak_source": peak_src + " HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "alg_bytes_per_launch": alg, "avg_launch_ms": ms, "launches": r["fine_launches"],
                     "limiter": "integer ALU and FP64 issue (instruction mix), not HBM",
@@ -821,11 +822,20 @@ def main():
     def want(f):
         return f in names
 
-    primary = timed(a.precision)
+    def ranged(name, fn, *args):
+        """fn(*args) inside an NVTX range named for the form (profiling:
+        ncu --nvtx --nvtx-include "<name>/")."""
+        torch.cuda.nvtx.range_push(name)
+        try:
+            return fn(*args)
+        finally:
+            torch.cuda.nvtx.range_pop()
+
+    primary = ranged("headline", timed, a.precision)
     second = None
     if want("mixed"):
-        second = timed("mixed" if a.precision == "fp64" else "fp64")
-    acc_form = at_accuracy(delta, a.rc) if want("accuracy") else None
+        second = ranged("mixed", timed, "mixed" if a.precision == "fp64" else "fp64")
+    acc_form = ranged("accuracy", at_accuracy, delta, a.rc) if want("accuracy") else None
     rc5_form = None
     if want("rc5") and a.pm_steps > 0 and a.rc != 5.0:
         # the run and the headline solve at H0 r_c = 5: its own z = 0 density
@@ -856,12 +866,12 @@ def main():
     if want("kmouflage") and a.pm_steps > 0:
         kmo_pos, pm_forms["gr_512mpch"] = pm_run(0.0, model=0, box=2.0 * a.box)
     e2e_primary = None if a.no_e2e else e2e(primary)
-    batch_form = batched() if (a.batch > 0 and want("batched")) else None
-    adj_form = adjoint() if (a.adj_ng > 0 and want("adjoint")) else None
-    pm_adj_form = adjoint_pm() if (a.pm_adj_ng > 0 and want("adjoint_pm")) else None
-    kmo_form = kmouflage(kmo_pos) if want("kmouflage") else None
+    batch_form = ranged("batched", batched) if (a.batch > 0 and want("batched")) else None
+    adj_form = ranged("adjoint", adjoint) if (a.adj_ng > 0 and want("adjoint")) else None
+    pm_adj_form = ranged("adjoint_pm", adjoint_pm) if (a.pm_adj_ng > 0 and want("adjoint_pm")) else None
+    kmo_form = ranged("kmouflage", kmouflage, kmo_pos) if want("kmouflage") else None
     kmo_pos = None
-    cyc_form = cycle_types() if want("cycles") else None
+    cyc_form = ranged("cycles", cycle_types) if want("cycles") else None
 
     if rank != 0:
         if dist:

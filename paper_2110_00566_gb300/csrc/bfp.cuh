@@ -267,6 +267,52 @@ __device__ __forceinline__ Sums stencil(const long long *Sm, const long long *S0
     return r;
 }
 
+// the central differences of the face neighbours (Kmouflage's gradient):
+// Delta_x = u(i+1) - u(i-1) etc., exact in the staged integers
+struct Diffs {
+    long long dx, dy, dz;
+};
+template <int TJ>
+__device__ __forceinline__ Diffs diffs(const long long *Sm, const long long *S0, const long long *Sp, int c, int jj,
+                                       int mm, int p)
+{
+    const int o = 1 - c;
+    Diffs d;
+    d.dx = at<TJ>(Sp, o, jj, mm) - at<TJ>(Sm, o, jj, mm);
+    d.dy = at<TJ>(S0, o, jj + 1, mm) - at<TJ>(S0, o, jj - 1, mm);
+    d.dz = at<TJ>(S0, o, jj, mm + p) - at<TJ>(S0, o, jj, mm + p - 1);
+    return d;
+}
+
+// N_K of the Kmouflage operator (Sec. 3.2.4, Eq. kmf_eqn_codeunit_final
+// over c~) from the staged integers: the linear parts -- Delta_a, the
+// combinations 2 S_a - S_b - S_c and C_ab -- exact integers rounded once to
+// binary64 at the scale ef, the rest in FP64:
+//   G^2 = sum_a Delta_a^2 / (4 h^2),
+//   T = sum_a Delta_a^2 (2 S_a - S_b - S_c) / (12 h^4) + sum_{a<b} C_ab Delta_a Delta_b / (8 h^4),
+//   N_K = (s - k3 (G^2)^(n-2) T) / (k1 + k2 (G^2)^(n-1))
+// (k1 = 1 + gamma (phibar'/H0)^(2(n-1)), k2 = (2n+1) gamma / 3,
+// k2 = 2 (n-1) gamma); the quotient by the corrected single-precision
+// reciprocal (k_quot: the denominator is at least 1)
+__device__ __forceinline__ double kmo64_N(const OpK<double> &op, const LevK<double> &L, const Sums &r, const Diffs &d,
+                                          double s, int ef)
+{
+    const double dx = fx_out(d.dx, ef), dy = fx_out(d.dy, ef), dz = fx_out(d.dz, ef);
+    const double px = fx_out(2 * r.X - r.Y - r.Z, ef), py = fx_out(2 * r.Y - r.X - r.Z, ef);
+    const double pz = fx_out(2 * r.Z - r.X - r.Y, ef);
+    const double cxy = fx_out(r.cxy, ef), cxz = fx_out(r.cxz, ef), cyz = fx_out(r.cyz, ef);
+    const double dx2 = dx * dx, dy2 = dy * dy, dz2 = dz * dz;
+    const double G2 = ((dx2 + dy2) + dz2) * L.g2s;
+    const double T1 = fma(dx2, px, fma(dy2, py, dz2 * pz));
+    const double T2 = fma(cxy, dx * dy, fma(cxz, dx * dz, cyz * (dy * dz)));
+    const double Tt = fma(L.td, T1, L.to * T2);
+    const double pw = ipow(G2, op.nkmo - 2);
+    const double B = fma(op.k2 * pw, G2, op.k1);
+    const double A = fma(-op.k3 * pw, Tt, s);
+    // (an IEEE quotient where B is beyond the reciprocal estimate's range)
+    return __double2hiint(B) < ((1023 + 1000) << 20) ? k_quot(A, B) : A / B;
+}
+
 // Q16 = 16 (a (a - b) + b^2) + 3 (C_xy^2 + C_xz^2 + C_yz^2) with a = X - Y,
 // b = X - Z, as 8 (a^2 + b^2 + (a - b)^2) + 3 (C_xy^2 + C_xz^2 + C_yz^2)
 // (16 (a^2 - a b + b^2) = 8 (2 a^2 + 2 b^2 - 2 a b)): six unsigned squares,

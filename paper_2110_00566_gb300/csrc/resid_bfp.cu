@@ -32,8 +32,9 @@ constexpr int RR_TJ = 8;   // tile rows: a warp covers 16 columns of two rows
 
 }
 
-// HASF: the level has a FAS source f (every level but the finest)
-template <bool RR, bool HASF>
+// HASF: the level has a FAS source f (every level but the finest); MODEL:
+// 0 nDGP, 1 Kmouflage
+template <bool RR, bool HASF, int MODEL>
 __global__ void __launch_bounds__(bfp::THREADS, 2)
 k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const double *__restrict__ S0,
             const double *__restrict__ S1, const double *__restrict__ F0, const double *__restrict__ F1, LevScal *sc,
@@ -114,9 +115,13 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
                 const bfp::Sums r = bfp::stencil<RR_TJ>(t.v[g.sm], t.v[g.s0], t.v[g.sp], c, jj, mm, p);
                 const long long U = bfp::at<RR_TJ>(t.v[g.s0], c, jj, mm);
                 Usum += U;
-                const double q = bfp::quad(r, g.ef);
                 const long long lap6 = (r.X + r.Y + r.Z) - ((U << 2) + (U << 1));   // |.| < 12 * 2^59
-                N = dgp64_N_any(op, dk, nk, q, s, cl);
+                if (MODEL == 0) {
+                    N = dgp64_N_any(op, dk, nk, bfp::quad(r, g.ef), s, cl);
+                } else {
+                    const bfp::Diffs dd = bfp::diffs<RR_TJ>(t.v[g.sm], t.v[g.s0], t.v[g.sp], c, jj, mm, p);
+                    N = bfp::kmo64_N(op, L, r, dd, s, g.ef);
+                }
                 if (FOLD)
                     d = fma(L.inv_h2, fx_out(lap6 + kv, g.ef), -N);
                 else
@@ -127,7 +132,14 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
                 gather(v, c ? U1 : U0, c ? U0 : U1, n, half, i, j, m, p);
                 const double u = __ldg((c ? U1 : U0) + rowi);
                 if (RR) su += u;
-                d = dgp64_resid(op, dk, nk, v, u, s, HASF ? F + rowi : nullptr, cshift, L.inv_h2, N, cl);
+                if (MODEL == 0) {
+                    d = dgp64_resid(op, dk, nk, v, u, s, HASF ? F + rowi : nullptr, cshift, L.inv_h2, N, cl);
+                } else {
+                    N = op_N<double, 1>(op, L, v, s, cl);
+                    const double S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
+                    d = (S6 - 6.0 * u) * L.inv_h2 - N + cshift;
+                    if (HASF) d -= fv[c];
+                }
             }
             acc[0] += N;
             acc[2] = fma(d, d, acc[2]);
@@ -194,7 +206,8 @@ static int bfp_planes(const LevArrays<double> &L, int cap)
 
 static bool bfp_eligible(const LevArrays<double> &L)
 {
-    return !L.base[0] && L.model == 0 && L.n >= 128 && L.half % bfp::TM == 0 && L.n % RR_TJ == 0;
+    return !L.base[0] && (L.model == 0 || L.model == 1) && L.n >= 128 && L.half % bfp::TM == 0 &&
+           L.n % RR_TJ == 0;
 }
 
 bool launch_resid_restrict_bfp(const LevArrays<double> &Lf, LevArrays<double> &Lc, const OpK<double> *op,
@@ -205,15 +218,18 @@ bool launch_resid_restrict_bfp(const LevArrays<double> &Lf, LevArrays<double> &L
     const dim3 b(bfp::THREADS, 1, 1);
     const dim3 g(Lf.half / bfp::TM, Lf.n / RR_TJ, (Lf.n + zc - 1) / zc);
     if ((long long)g.x * g.y * g.z > rb.cap) return false;
-#define MG_RRB(HASF)                                                                                         \
-    k_resid_bfp<true, HASF><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb,   \
+#define MG_RRB(HASF, MODEL)                                                                                  \
+    k_resid_bfp<true, HASF, MODEL><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb,   \
                                              make_levk<double>(Lf.n, Lf.h), op, Lc.U(0), Lc.U(1), Lc.ur[0],      \
                                              Lc.ur[1], Lc.fbuf[0], Lc.fbuf[1], nullptr, nullptr,                \
                                              make_dgpk64(Lf.h), zc)
-    if (Lf.f[0])
-        MG_RRB(true);
-    else
-        MG_RRB(false);
+    if (Lf.model == 0) {
+        if (Lf.f[0]) MG_RRB(true, 0);
+        else MG_RRB(false, 0);
+    } else {
+        if (Lf.f[0]) MG_RRB(true, 1);
+        else MG_RRB(false, 1);
+    }
 #undef MG_RRB
     return true;
 }
@@ -226,15 +242,18 @@ bool launch_resid_norm_bfp(const LevArrays<double> &L, const OpK<double> *op, co
     const dim3 b(bfp::THREADS, 1, 1);
     const dim3 g(L.half / bfp::TM, L.n / RR_TJ, (L.n + zc - 1) / zc);
     if ((long long)g.x * g.y * g.z > rb.cap) return false;
-#define MG_RNB(HASF)                                                                                          \
-    k_resid_bfp<false, HASF><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb,           \
+#define MG_RNB(HASF, MODEL)                                                                                   \
+    k_resid_bfp<false, HASF, MODEL><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb,           \
                                               make_levk<double>(L.n, L.h), op, nullptr, nullptr, nullptr, nullptr, \
                                               nullptr, nullptr, D ? D[0] : nullptr, D ? D[1] : nullptr,           \
                                               make_dgpk64(L.h), zc)
-    if (L.f[0])
-        MG_RNB(true);
-    else
-        MG_RNB(false);
+    if (L.model == 0) {
+        if (L.f[0]) MG_RNB(true, 0);
+        else MG_RNB(false, 0);
+    } else {
+        if (L.f[0]) MG_RNB(true, 1);
+        else MG_RNB(false, 1);
+    }
 #undef MG_RNB
     return true;
 }

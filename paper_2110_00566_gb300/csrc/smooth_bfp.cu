@@ -18,19 +18,18 @@ namespace mg {
 namespace {
 constexpr int SM_TJ = 16;   // tile rows: each thread updates rows ty and ty + 8
 
-// the update where the level's constant is not folded into S6 / 6 (a FAS
-// source, or a constant beyond the block's scale), out of line so that the
-// compiler does not predicate it into every cell
-__device__ __noinline__ double smooth_unfolded(const OpK<double> &op, const DgpK64 &dk, const NtK &nk, double q,
-                                               double s, long long s6, int ef, double fcf)
+// the update where the level's constant does not fit the block's scale
+// (rare), out of line so that the compiler does not predicate it into every
+// cell
+__device__ __noinline__ double smooth_unfolded(double mh6, double N, double fcf, long long s6, int ef)
 {
-    int cl = 0;
-    return dgp64_finish(op, dk, nk, q, s, fx_out(s6, ef), fcf, cl);
+    return fma(mh6, N + fcf, fx_out(s6, ef));
 }
 }
 
-// HASF: the level has a FAS source f (every level but the finest)
-template <bool HASF>
+// HASF: the level has a FAS source f (every level but the finest); MODEL:
+// 0 nDGP (Eq. nonlinear_GS_DGP), 1 Kmouflage (the same update with N_K)
+template <bool HASF, int MODEL>
 __global__ void __launch_bounds__(bfp::THREADS, 2)
 k_smooth_bfp(const double *__restrict__ Uc, const double *__restrict__ Uo, double *__restrict__ Un,
              const double *__restrict__ Sc, const double *__restrict__ Fc, const LevScal *__restrict__ sc,
@@ -89,18 +88,30 @@ k_smooth_bfp(const double *__restrict__ Uc, const double *__restrict__ Uo, doubl
             int cl = 0;
             if (fx_ok(g.ef)) {
                 const bfp::Sums r = bfp::stencil<SM_TJ>(t.v[g.sm], t.v[g.s0], t.v[g.sp], 0, jj, mm, p);
-                const double q = bfp::quad(r, g.ef);
                 const long long s6 = fx_div6(r.X + r.Y + r.Z);
+                double N;
+                if (MODEL == 0) {
+                    N = dgp64_N_any(op, dk, nk, bfp::quad(r, g.ef), sv[h], cl);
+                } else {
+                    const bfp::Diffs dd = bfp::diffs<SM_TJ>(t.v[g.sm], t.v[g.s0], t.v[g.sp], 0, jj, mm, p);
+                    N = bfp::kmo64_N(op, L, r, dd, sv[h], g.ef);
+                }
                 if (HASF)
-                    out = dgp64_finish(op, dk, nk, q, sv[h], fx_out(s6, g.ef), fcf, cl);
+                    out = fma(dk.mh6, N + fcf, fx_out(s6, g.ef));
                 else if (fold)
-                    out = fma(dk.mh6, dgp64_N_any(op, dk, nk, q, sv[h], cl), fx_out(s6 + kv, g.ef));
+                    out = fma(dk.mh6, N, fx_out(s6 + kv, g.ef));
                 else
-                    out = smooth_unfolded(op, dk, nk, q, sv[h], s6, g.ef, fcf);
+                    out = smooth_unfolded(dk.mh6, N, fcf, s6, g.ef);
             } else {
                 Nb<double> v;
                 gather(v, Uc, Uo, n, half, i, j, m, p);
-                out = dgp64_update(op, dk, nk, v, sv[h], fcf, cl);
+                if (MODEL == 0) {
+                    out = dgp64_update(op, dk, nk, v, sv[h], fcf, cl);
+                } else {
+                    const double N = op_N<double, 1>(op, L, v, sv[h], cl);
+                    const double S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
+                    out = (S6 - L.h2 * (N + fcf)) * (1.0 / 6.0);
+                }
             }
             Un[base + h * rows8] = out;
         }
@@ -118,18 +129,24 @@ k_smooth_bfp(const double *__restrict__ Uc, const double *__restrict__ Uo, doubl
 bool launch_smooth_bfp(const LevArrays<double> &L, const LevK<double> &K, const OpK<double> *op, int colour, int nb,
                        cudaStream_t st)
 {
-    if (L.base[0] || L.model != 0 || L.n < 128 || L.half % bfp::TM != 0 || L.n % SM_TJ != 0) return false;
+    if (L.base[0] || (L.model != 0 && L.model != 1) || L.n < 128 || L.half % bfp::TM != 0 || L.n % SM_TJ != 0)
+        return false;
     const long long tiles = (long long)(L.half / bfp::TM) * (L.n / SM_TJ);
     int zc = 16;
     while (zc > 2 && tiles * ((L.n + zc - 1) / zc) < 600) zc /= 2;
     const dim3 b(bfp::TM, bfp::THREADS / bfp::TM, 1);
     const dim3 g(L.half / bfp::TM, L.n / SM_TJ, (L.n + zc - 1) / zc);
-    if (L.f[colour])
-        k_smooth_bfp<true><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], L.f[colour],
-                                            L.sc, K, op, colour, make_dgpk64(L.h), zc);
-    else
-        k_smooth_bfp<false><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour], nullptr,
-                                             L.sc, K, op, colour, make_dgpk64(L.h), zc);
+#define MG_SBF(HASF, MODEL)                                                                                    \
+    k_smooth_bfp<HASF, MODEL><<<g, b, 0, st>>>(L.U(colour), L.U(1 - colour), L.u[nb][colour], L.s[colour],         \
+                                               L.f[colour], L.sc, K, op, colour, make_dgpk64(L.h), zc)
+    if (L.model == 0) {
+        if (L.f[colour]) MG_SBF(true, 0);
+        else MG_SBF(false, 0);
+    } else {
+        if (L.f[colour]) MG_SBF(true, 1);
+        else MG_SBF(false, 1);
+    }
+#undef MG_SBF
     return true;
 }
 
