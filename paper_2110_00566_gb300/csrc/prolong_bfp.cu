@@ -28,7 +28,7 @@ constexpr int PC_TJ = PF_TJ / 2;          // coarse rows per tile
 constexpr int PC_TM = bfp::TM / 2;        // coarse split columns per tile
 }
 
-__global__ void __launch_bounds__(bfp::THREADS, 2)
+__global__ void __launch_bounds__(bfp::THREADS, 4)
 k_prolong_bfp(double *U0, double *U1, const double *__restrict__ E0, const double *__restrict__ E1, int n, int zc)
 {
     __shared__ bfp::Shared<PC_TJ, PC_TM> t;

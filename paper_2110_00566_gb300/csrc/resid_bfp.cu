@@ -35,7 +35,7 @@ constexpr int RR_TJ = 8;   // tile rows: a warp covers 16 columns of two rows
 // HASF: the level has a FAS source f (every level but the finest); MODEL:
 // 0 nDGP, 1 Kmouflage
 template <bool RR, bool HASF, int MODEL>
-__global__ void __launch_bounds__(bfp::THREADS, 2)
+__global__ void __launch_bounds__(bfp::THREADS, 3)
 k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const double *__restrict__ S0,
             const double *__restrict__ S1, const double *__restrict__ F0, const double *__restrict__ F1, LevScal *sc,
             RedBuf rb, LevK<double> L, const OpK<double> *__restrict__ opp, double *__restrict__ Uc0,
