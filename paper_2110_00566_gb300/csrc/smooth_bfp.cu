@@ -30,7 +30,7 @@ __device__ __noinline__ double smooth_unfolded(double mh6, double N, double fcf,
 // HASF: the level has a FAS source f (every level but the finest); MODEL:
 // 0 nDGP (Eq. nonlinear_GS_DGP), 1 Kmouflage (the same update with N_K)
 template <bool HASF, int MODEL>
-__global__ void __launch_bounds__(bfp::THREADS, 3)
+__global__ void __launch_bounds__(bfp::THREADS, 4)
 k_smooth_bfp(const double *__restrict__ Uc, const double *__restrict__ Uo, double *__restrict__ Un,
              const double *__restrict__ Sc, const double *__restrict__ Fc, const LevScal *__restrict__ sc,
              LevK<double> L, const OpK<double> *__restrict__ opp, int colour, DgpK64 dk, int zc)

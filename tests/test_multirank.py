@@ -47,7 +47,7 @@ def test_reduce_without_process_group_is_identity():
 
 
 class A:
-    ng, np, box, rc, rtol, steps, warmup = 16, 8, 16.0, 1.0, 1e-8, 1, 1
+    ng, np, box, rc, rtol, steps, warmup, pm_steps = 16, 8, 16.0, 1.0, 1e-8, 1, 1, 0
 
 
 def test_ranks_solve_different_instances():
