@@ -1,0 +1,128 @@
+"""Degenerate and edge cases of the solve on the GPU path, with the meshes
+of 128^3 and more that run the block-staged FP64 kernels:
+
+* delta = 0 and delta = const: the mean-subtracted source vanishes, the
+  initial residual is exactly zero and phi = 0 is returned after no cycle;
+* a uniform-density relaxation (Sec. 4.2.1: delta = 0 with a U[-0.05, 0.05]
+  initial guess) reaches phi = 0 to 1e-12;
+* voids: delta = -1 on most cells and a few dense clumps (the largest
+  contrast the CIC density allows), against the oracle;
+* the extremes of the model parameter (H0 r_c = 0.1, strongly coupled, and
+  1000, nearly GR) against the oracle;
+* the smallest mesh (8^3: one level above the 4^3 coarsest) in FP64 and
+  mixed precision against the oracle;
+* complete 128^3 solves (FP64, mixed, Kmouflage) element by element against
+  the oracle's solution."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_00566_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from test_gpu_parity import B, ctx  # noqa: E402,F401
+
+
+def l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def solve(B, ctx, delta, rc=1.0, prec=0, rtol=1e-10, atol=0.0, phi=None, warm=0, max_cycles=60):
+    n = delta.shape[0]
+    phi = np.zeros_like(delta) if phi is None else phi
+    code, st = B.mg_solve_dgp(ctx, [dict(ng=n, box_mpch=float(n), a=1.0, omega_m=0.3, rc_h0=rc, delta=delta,
+                                         phi=phi)],
+                              B.opts(rtol=rtol, atol=atol, precision=prec, warm_start=warm, max_cycles=max_cycles))
+    return phi, code, st[0]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("value", [0.0, 2.5])
+def test_constant_density_gives_zero_field(B, ctx, prec, value):
+    n = 128
+    delta = np.full((n,) * 3, value)
+    phi, code, st = solve(B, ctx, delta, prec=prec, rtol=1e-8)
+    assert code == 0 and st.cycles == 0
+    assert np.array_equal(phi, np.zeros_like(phi))
+
+
+def test_uniform_relaxation_on_the_staged_kernels(B, ctx):
+    n = 128
+    u0 = inputs.uniform_guess(n, 1)
+    phi, code, st = solve(B, ctx, np.zeros((n,) * 3), rtol=0.0, atol=1e-16, phi=u0, warm=1)
+    assert code == 0 and st.cycles > 0
+    assert np.abs(phi).max() < 1e-12
+
+
+def voids(n, seed):
+    """delta = -1 except for a few clumps of particles (CIC-deposited), the
+    largest density contrast a particle load produces."""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0, n, size=(6, 3))
+    pts = np.concatenate([c + rng.normal(0, 0.8, size=(400, 3)) for c in centres])
+    pos = np.mod(pts, n).astype(np.float32)
+    pos[pos >= n] -= np.float32(n)
+    nps = round(pos.shape[0] ** (1 / 3))
+    delta, _ = oracle.cic_deposit(pos, n, nps)
+    # the oracle's normalisation assumes nps^3 particles: rescale to mean 0
+    rho = delta + 1.0
+    return rho / rho.mean() - 1.0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_voids_and_clumps(B, ctx, prec):
+    n = 32
+    delta = voids(n, 11)
+    assert delta.min() == pytest.approx(-1.0) and delta.max() > 100
+    ref, _ = oracle.dgp_solve(delta, 1.0, 0.3, 1.0, oracle.Opts(rtol=1e-11, max_cycles=60))
+    phi, code, _ = solve(B, ctx, delta, prec=prec)
+    assert code == 0 and l2(phi, ref) < 1e-6, l2(phi, ref)
+
+
+@pytest.mark.parametrize("rc", [0.1, 1000.0])
+def test_extreme_crossover_scales(B, ctx, rc):
+    n = 32
+    delta = 2.0 * inputs.white_noise(n, 21)
+    delta = np.maximum(delta, -1.0)
+    ref, _ = oracle.dgp_solve(delta, 1.0, 0.3, rc, oracle.Opts(rtol=1e-11, max_cycles=60))
+    phi, code, _ = solve(B, ctx, delta, rc=rc)
+    assert code == 0 and l2(phi, ref) < 1e-6, l2(phi, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_smallest_mesh(B, ctx, prec):
+    n = 8
+    delta = np.maximum(1.5 * inputs.white_noise(n, 31), -1.0)
+    ref, _ = oracle.dgp_solve(delta, 1.0, 0.3, 1.0, oracle.Opts(rtol=1e-11, max_cycles=60))
+    phi, code, _ = solve(B, ctx, delta, prec=prec)
+    assert code == 0 and l2(phi, ref) < 1e-6, l2(phi, ref)
+
+
+@pytest.fixture(scope="module")
+def field128():
+    n = 128
+    pos, _ = inputs.zeldovich(n // 2, n, float(n), inputs.pk_cutoff(0.96, 5.0, 0.8), 1.0, seed=41)
+    delta, _ = oracle.cic_deposit(pos, n, n // 2)
+    return delta
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_128_solve_against_the_oracle(B, ctx, field128, prec):
+    ref, rst = oracle.dgp_solve(field128, 1.0, 0.3, 1.0, oracle.Opts(rtol=1e-11, max_cycles=60))
+    phi, code, st = solve(B, ctx, field128, prec=prec, rtol=1e-11)
+    assert code == 0 and l2(phi, ref) < 1e-8, l2(phi, ref)
+    assert abs(st.eps_ref - rst.eps_ref) < 1e-12 * rst.eps_ref
+
+
+def test_full_128_kmouflage_solve_against_the_oracle(B, ctx, field128):
+    n, box, a, om = 128, 128.0, 1.0, 0.3
+    lam = np.sqrt(3 * (1 - om))
+    pars = (box, 2, 1.0, 0.2, lam, -1e-3, np.exp(-0.02))
+    delta = 20.0 * field128
+    ref, _ = oracle.kmo_solve(delta, a, om, *pars, oracle.Opts(rtol=1e-10, max_cycles=60))
+    phi = np.zeros_like(delta)
+    code, _ = B.mg_solve_kmouflage(ctx, n, box, a, om, 2, 1.0, 0.2, lam, -1e-3, np.exp(-0.02), delta, phi,
+                                   B.opts(rtol=1e-10, max_cycles=60))
+    assert code == 0 and l2(phi, ref) < 1e-8, l2(phi, ref)
