@@ -314,15 +314,52 @@ __device__ __forceinline__ double kmo64_N(const OpK<double> &op, const LevK<doub
 }
 
 // Q16 = 16 (a (a - b) + b^2) + 3 (C_xy^2 + C_xz^2 + C_yz^2) with a = X - Y,
-// b = X - Z, as 8 (a^2 + b^2 + (a - b)^2) + 3 (C_xy^2 + C_xz^2 + C_yz^2)
-// (16 (a^2 - a b + b^2) = 8 (2 a^2 + 2 b^2 - 2 a b)): six unsigned squares,
-// exact in 128 bits, rounded once to binary64 at the scale ef
+// b = X - Z, as 8 G_A + 3 G_C, G_A = a^2 + b^2 + (a - b)^2 and G_C = C_xy^2 +
+// C_xz^2 + C_yz^2 (16 (a^2 - a b + b^2) = 8 (2 a^2 + 2 b^2 - 2 a b)), exact in
+// 128 bits and rounded once to binary64 at the scale ef.  Each difference
+// (|d| < 2^61) is split into 31-bit limbs, d = dh 2^31 + dl with dl in
+// [0, 2^31) and |dh| <= 2^30, so d^2 = dh^2 2^62 + dh dl 2^32 + dl^2; over a
+// group of three the limb products sum exactly in 64 bits (sum dh^2 <=
+// 3 2^60, |sum dh dl| < 3 2^61, sum dl^2 < 3 2^62), one 32 x 32 -> 64-bit
+// multiply-add each, and the group is assembled in 128 bits once
+struct Limbs {
+    long long p2 = 0, p1 = 0;
+    unsigned long long p0 = 0;
+};
+__device__ __forceinline__ void sq_acc(Limbs &g, long long d)
+{
+    const unsigned lo = (unsigned)d, hi = (unsigned)((unsigned long long)d >> 32);
+    const int dh = (int)__funnelshift_r(lo, hi, 31);   // bits 31..62: d >> 31 for |d| < 2^62
+    const int dl = (int)(lo & 0x7FFFFFFFu);
+    g.p2 += (long long)dh * dh;
+    g.p1 += (long long)dh * dl;
+    g.p0 += (unsigned long long)(unsigned)dl * (unsigned)dl;
+}
+// p2 2^62 + p1 2^32 + p0 modulo 2^128 (p1 signed, the total non-negative)
+__device__ __forceinline__ U128 limbs128(const Limbs &g)
+{
+    const U128 t1{(unsigned long long)g.p1 << 32, (unsigned long long)(g.p1 >> 32)};
+    const U128 t2{(unsigned long long)g.p2 << 62, (unsigned long long)g.p2 >> 2};
+    return add128(add128(U128{g.p0, 0ull}, t1), t2);
+}
 __device__ __forceinline__ double quad(const Sums &r, int ef)
 {
-    const long long a = r.X - r.Y, b = r.X - r.Z, amb = r.Z - r.Y;
-    const U128 A = add128(add128(sqr_s64(a), sqr_s64(b)), sqr_s64(amb));
-    const U128 C = add128(add128(sqr_s64(r.cxy), sqr_s64(r.cxz)), sqr_s64(r.cyz));
-    return fx_out_q(add128(shl128(A, 3), add128(C, shl128(C, 1))), ef);
+    U128 GA, GC;
+    {
+        Limbs A;
+        sq_acc(A, r.X - r.Y);
+        sq_acc(A, r.X - r.Z);
+        sq_acc(A, r.Z - r.Y);
+        GA = limbs128(A);
+    }
+    {
+        Limbs C;
+        sq_acc(C, r.cxy);
+        sq_acc(C, r.cxz);
+        sq_acc(C, r.cyz);
+        GC = limbs128(C);
+    }
+    return fx_out_q(add128(shl128(GA, 3), add128(GC, shl128(GC, 1))), ef);
 }
 
 }  // namespace bfp
