@@ -406,22 +406,21 @@ static int solve_plain(mg_ctx *ctx, int n, const ModelDesc &md, const double *de
     const long long per_cycle = cycle_updates(P, o, 0, o.cycle);
     int cyc = 0, norms = 0;
     bool conv = eps <= o.rtol * eps_ref + o.atol;
-    // The finest residual norm costs about a sweep: it is measured after the
-    // first cycle, then whenever the residual predicted with half the
-    // observed per-cycle reduction rate is within a factor 10 of the
-    // tolerance, and at least every third cycle.  The optimistic prediction
-    // never skips a cycle at which the real residual has reached the
-    // tolerance (as long as the rate does not improve more than twofold), so
-    // no cycle is wasted; unmeasured cycles take c from their own
-    // residual/restriction pass.  Convergence is only declared on a measured
-    // residual.
+    // The finest residual norm costs about two half-sweeps: it is measured
+    // after the first cycle, then whenever the residual predicted with half
+    // the observed per-cycle reduction rate reaches the tolerance, and at
+    // least every third cycle.  The optimistic prediction never skips a cycle
+    // at which the real residual has reached the tolerance (as long as the
+    // rate does not improve more than twofold), so no cycle is wasted;
+    // unmeasured cycles take c from their own residual/restriction pass.
+    // Convergence is only declared on a measured residual.
     const double target = o.rtol * eps_ref + o.atol;
     double rho = 0.05, eps_meas = eps;
     int since = 0;
     while (!conv && cyc < o.max_cycles) {
         ++since;
         const double predicted = eps_meas * std::pow(rho, since);
-        const bool measure = cyc == 0 || predicted <= 10.0 * target || since >= 3 || cyc + 1 == o.max_cycles;
+        const bool measure = cyc == 0 || predicted <= target || since >= 3 || cyc + 1 == o.max_cycles;
         cycle_and_norm(ctx, P, o, measure);
         ++cyc;
         if (ctx->prof_on) {

@@ -12,7 +12,10 @@ of 128^3 and more that run the block-staged FP64 kernels:
 * the smallest mesh (8^3: one level above the 4^3 coarsest) in FP64 and
   mixed precision against the oracle;
 * complete 128^3 solves (FP64, mixed, Kmouflage) element by element against
-  the oracle's solution."""
+  the oracle's solution;
+* the FP64 solve, which measures its residual norm only on the cycles its
+  rate prediction selects, stops at the same cycle as the oracle, which
+  measures every cycle (no cycle wasted, none skipped)."""
 import numpy as np
 import pytest
 
@@ -114,6 +117,24 @@ def test_full_128_solve_against_the_oracle(B, ctx, field128, prec):
     phi, code, st = solve(B, ctx, field128, prec=prec, rtol=1e-11)
     assert code == 0 and l2(phi, ref) < 1e-8, l2(phi, ref)
     assert abs(st.eps_ref - rst.eps_ref) < 1e-12 * rst.eps_ref
+    if prec == 0:
+        assert st.cycles == rst.cycles
+
+
+@pytest.mark.parametrize("n", [32, 64])
+@pytest.mark.parametrize("rc", [1.0, 5.0])
+@pytest.mark.parametrize("rtol", [1e-6, 1e-8, 1e-10])
+def test_norm_schedule_stops_at_the_oracles_cycle(B, ctx, n, rc, rtol):
+    pos, _ = inputs.zeldovich(n // 2, n, float(n), inputs.pk_cutoff(0.96, 5.0, 0.8), 1.0, seed=7 + n)
+    delta, _ = oracle.cic_deposit(pos, n, n // 2)
+    _, rst = oracle.dgp_solve(delta, 1.0, 0.3, rc, oracle.Opts(rtol=rtol, max_cycles=60))
+    target = rtol * rst.eps_ref
+    k = rst.cycles
+    # (a case whose residual lands within 1e-6 of the tolerance could
+    # legitimately stop a cycle apart on the two sides)
+    assert abs(rst.eps[k] - target) > 1e-6 * target and abs(rst.eps[k - 1] - target) > 1e-6 * target
+    _, code, st = solve(B, ctx, delta, rc=rc, rtol=rtol)
+    assert code == 0 and st.cycles == k, (st.cycles, k)
 
 
 def test_full_128_kmouflage_solve_against_the_oracle(B, ctx, field128):
