@@ -142,12 +142,12 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
                 }
             }
             acc[0] += N;
-            acc[2] = fma(d, d, acc[2]);
             nclamp += cl;
             if (RR) {
                 sd += d;
             } else {
                 acc[1] += d;
+                acc[2] = fma(d, d, acc[2]);
                 if (D0) (c ? D1 : D0)[rowi] = (float)(-d);
             }
         }
@@ -171,7 +171,6 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
                 (C ? Uc1 : Uc0)[cidx] = Ru;
                 (C ? URc1 : URc0)[cidx] = Ru;
                 (C ? RDc1 : RDc0)[cidx] = sd * 0.125;
-                acc[1] += sd;
             }
             sd = 0.0;
             su = 0.0;
@@ -188,7 +187,9 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
         const double dc = c_new - c_old;
         set_c(sc, c_new);
         sc->dc = dc;
-        sc->eps2 = (tot[2] + 2.0 * dc * tot[1] + cnt * dc * dc) / cnt;
+        // (the restriction pass sums neither d nor d^2: its residual norm is
+        // not used, and the norm pass gives it where it is)
+        sc->eps2 = RR ? __longlong_as_double(0x7FF8000000000000LL) : (tot[2] + 2.0 * dc * tot[1] + cnt * dc * dc) / cnt;
         sc->sumN = tot[0];
         sc->clamps = tot[3];
     }

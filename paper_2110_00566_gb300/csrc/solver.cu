@@ -1077,6 +1077,16 @@ static int op_resid_restrict_t(mg_ctx *ctx, const mg_op_params *op, int n, doubl
     launch_resid_restrict<T>(L, C, P.opT, P.rb, st);
     LevScal hs;
     read_scal(ctx, L.sc, &hs);
+    // the residual norm (with the compatibility constant the restriction
+    // pass set) from the norm pass: the restriction pass of the V-cycle does
+    // not sum d^2
+    double eps2 = hs.eps2;
+    if (eps_out) {
+        launch_resid_norm<T>(L, P.opT, P.rb, st);
+        LevScal hn;
+        read_scal(ctx, L.sc, &hn);
+        eps2 = hn.eps2;
+    }
     T *ru[2] = {C.U(0), C.U(1)};
     launch_merge<T>(ru, n / 2, Ru, nullptr, st);
     ctx->hpin[0] = -hs.dc;
@@ -1084,7 +1094,7 @@ static int op_resid_restrict_t(mg_ctx *ctx, const mg_op_params *op, int n, doubl
     launch_merge<T>(C.fbuf, n / 2, Rd, ctx->dscratch, st);
     MG_CK(cudaStreamSynchronize(st));
     if (c_out) *c_out = hs.c;
-    if (eps_out) *eps_out = std::sqrt(std::fmax(hs.eps2, 0.0));
+    if (eps_out) *eps_out = std::sqrt(std::fmax(eps2, 0.0));
     return MG_OK;
 }
 
