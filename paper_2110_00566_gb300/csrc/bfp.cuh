@@ -33,14 +33,13 @@ constexpr int W = TM + 2;               // with the k+-1 halo columns
 constexpr int THREADS = 256;
 
 // a tile of TMc split-index columns and TJ rows with a one-cell halo: values
-// per colour and plane, values staged per plane (both colours) and per thread
+// per colour and plane, values staged per plane (both colours)
 template <int TJ, int TMc = TM>
 struct Tile {
     static constexpr int Wc = TMc + 2;
     static constexpr int H = TJ + 2;
     static constexpr int PLANE = Wc * H;
     static constexpr int LOAD = 2 * PLANE;
-    static constexpr int PER = (LOAD + THREADS - 1) / THREADS;
 };
 
 template <int TJ, int TMc = TM>
@@ -84,57 +83,59 @@ __device__ __forceinline__ long long at(const long long *slot, int c, int r, int
 }
 
 // S: guard bits of the conversion (fixsum.cuh): 6 for the stencil sums
-// (|V| < 2^59), 3 where 64 values are summed with integer weights
+// (|V| < 2^59), 3 where 64 values are summed with integer weights.  Each half
+// of the block stages one colour: thread tid holds elements
+// e = tid % HT + q HT (q < PC) of colour tid / HT's plane, so that its global
+// array and shared-memory row are fixed and only the last element can fall
+// outside the plane.
 template <int TJ, int TMc = TM, int S = 6>
 struct Stager {
-    static constexpr int PLANE = Tile<TJ, TMc>::PLANE, LOAD = Tile<TJ, TMc>::LOAD, PER = Tile<TJ, TMc>::PER;
+    static constexpr int PLANE = Tile<TJ, TMc>::PLANE, LOAD = Tile<TJ, TMc>::LOAD;
     static constexpr int Wc = Tile<TJ, TMc>::Wc;
+    static constexpr int HT = THREADS / 2;               // threads per colour
+    static constexpr int PC = (PLANE + HT - 1) / HT;     // elements per thread
     Shared<TJ, TMc> &t;
-    const double *A0, *A1;   // the colour arrays staged as colour slots 0 and 1
-    int n, tid;
+    const double *A;         // this thread's colour array
+    int n, tid, sb;          // sb: shared-memory index of element q = 0
     long long pstride;
-    int goff[PER];
-    unsigned ocol;           // bit q: element q comes from A1
-    double x[PER];           // a plane in flight
+    int goff[PC];
+    double x[PC];            // a plane in flight
     int E = 0;               // the staged planes' largest exponent field (0: all zero)
     int ef = 1023 << 20;     // the conversion scale
     int sm = 0, s0 = 1, sp = 2;
 
-    // element e = tid + q * THREADS of a plane is colour e / PLANE, tile row
-    // jj, column mm: row j0 - 1 + jj and split index m0 - 1 + mm (wrapped)
+    // element e of colour c is tile row jj = e / Wc, column mm = e % Wc: row
+    // j0 - 1 + jj and split index m0 - 1 + mm (wrapped)
     __device__ Stager(Shared<TJ, TMc> &sh, const double *a0, const double *a1, int n_, int half, int m0, int j0,
                       int tid_)
-        : t(sh), A0(a0), A1(a1), n(n_), tid(tid_), pstride((long long)n_ * half), ocol(0)
+        : t(sh), A((tid_ / HT) ? a1 : a0), n(n_), tid(tid_), sb((tid_ / HT) * PLANE + tid_ % HT),
+          pstride((long long)n_ * half)
     {
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int e = tid + q * THREADS;
-            const int ee = e < LOAD ? e : 0;
-            const int col = ee >= PLANE;
-            const int r = ee - col * PLANE;
-            const int jj = r / Wc, mm = r - jj * Wc;
+        for (int q = 0; q < PC; ++q) {
+            const int e = tid % HT + q * HT;
+            const int ee = e < PLANE ? e : 0;
+            const int jj = ee / Wc, mm = ee - jj * Wc;
             int j = j0 - 1 + jj, m = m0 - 1 + mm;
             j = j < 0 ? j + n : (j >= n ? j - n : j);
             m = m < 0 ? m + half : (m >= half ? m - half : m);
             goff[q] = j * half + m;
-            ocol |= (unsigned)col << q;
         }
     }
+    // element q lies in the plane (always for q < PC - 1)
+    __device__ bool in(int q) const { return q < PC - 1 || tid % HT + q * HT < PLANE; }
     __device__ int wrap(int i) const { return i < 0 ? i + n : (i >= n ? i - n : i); }
     __device__ void prefetch(int ip)
     {
-        const long long base = (long long)wrap(ip) * pstride;
+        const double *Ap = A + (long long)wrap(ip) * pstride;
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int e = tid + q * THREADS;
-            x[q] = e < LOAD ? __ldg(((ocol >> q) & 1 ? A1 : A0) + base + goff[q]) : 0.0;
-        }
+        for (int q = 0; q < PC; ++q) x[q] = in(q) ? __ldg(Ap + goff[q]) : 0.0;
     }
     __device__ int xmax() const
     {
         int e = 0;
 #pragma unroll
-        for (int q = 0; q < PER; ++q) e = max(e, ef_of(x[q]));
+        for (int q = 0; q < PC; ++q) e = max(e, ef_of(x[q]));
         return e;
     }
     __device__ void block_max(int slot, int e)
@@ -144,11 +145,10 @@ struct Stager {
     }
     __device__ void store(int s)
     {
+        long long *d = t.v[s] + sb;
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int e = tid + q * THREADS;
-            if (e < LOAD) t.v[s][e] = fx_in<S>(x[q], ef);
-        }
+        for (int q = 0; q < PC; ++q)
+            if (in(q)) d[q * HT] = fx_in<S>(x[q], ef);
     }
     __device__ void shift_down(int s, unsigned d)
     {
@@ -158,12 +158,11 @@ struct Stager {
     // the next plane, so this thread's elements are read one at a time)
     __device__ void reconvert(int s, int ip)
     {
-        const long long base = (long long)wrap(ip) * pstride;
+        const double *Ap = A + (long long)wrap(ip) * pstride;
+        long long *d = t.v[s] + sb;
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int e = tid + q * THREADS;
-            if (e < LOAD) t.v[s][e] = fx_in<S>(__ldg(((ocol >> q) & 1 ? A1 : A0) + base + goff[q]), ef);
-        }
+        for (int q = 0; q < PC; ++q)
+            if (in(q)) d[q * HT] = fx_in<S>(__ldg(Ap + goff[q]), ef);
     }
     // planes i0 - 1, i0, i0 + 1 into slots 0, 1, 2; each plane's maximum is
     // reduced on its own (reduction slot q & 1; the other slot, read before
@@ -175,7 +174,7 @@ struct Stager {
             t.emax[1] = 0;
         }
         __syncthreads();
-        double xs[2][PER];
+        double xs[2][PC];
         for (int q3 = 0; q3 < 3; ++q3) {
             prefetch(i0 + q3 - 1);
             block_max(q3 & 1, xmax());
@@ -189,16 +188,16 @@ struct Stager {
             E = max(E, e3);
             if (q3 < 2) {
 #pragma unroll
-                for (int q = 0; q < PER; ++q) xs[q3][q] = x[q];
+                for (int q = 0; q < PC; ++q) xs[q3][q] = x[q];
             }
         }
         ef = fx_zero_scale(E);
         store(2);
 #pragma unroll
-        for (int q = 0; q < PER; ++q) x[q] = xs[0][q];
+        for (int q = 0; q < PC; ++q) x[q] = xs[0][q];
         store(0);
 #pragma unroll
-        for (int q = 0; q < PER; ++q) x[q] = xs[1][q];
+        for (int q = 0; q < PC; ++q) x[q] = xs[1][q];
         store(1);
         if (tid == 0) t.emax[0] = 0;   // slot 0, last read before the fill's final barrier
         __syncthreads();
