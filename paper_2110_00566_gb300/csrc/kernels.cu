@@ -458,6 +458,8 @@ template <typename T>
 void launch_coarse_source(const LevArrays<T> &Lf, const LevArrays<T> &Lc, const OpK<T> *op, const RedBuf &rb,
                           cudaStream_t st)
 {
+    if constexpr (sizeof(T) == 8)
+        if (launch_coarse_source_bfp(Lf, Lc, op, rb, st)) return;
     const dim3 b = block_mj(Lc.half);
     dim3 g = grid_mj(Lc.half, Lc.n, b, 1);
     g.z = red_z(g, 2 * Lc.n, rb.cap);

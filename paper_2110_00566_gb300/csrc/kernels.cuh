@@ -56,6 +56,11 @@ bool launch_resid_restrict_bfp(const LevArrays<double> &Lf, LevArrays<double> &L
                                const RedBuf &rb, cudaStream_t st);
 bool launch_resid_norm_bfp(const LevArrays<double> &L, const OpK<double> *op, const RedBuf &rb, cudaStream_t st,
                            float *const *D);
+// the coarse level's FAS source (Eq. general_pde_numerical_coarse) on the
+// block-staged kernel (resid_bfp.cu); false when the coarse level is not
+// eligible
+bool launch_coarse_source_bfp(const LevArrays<double> &Lf, const LevArrays<double> &Lc, const OpK<double> *op,
+                              const RedBuf &rb, cudaStream_t st);
 // FP64 prolongation of the coarse correction held in Lc.ur (formed by the
 // coarse-correction pass) with the coarse planes staged in shared memory as
 // block fixed point (prolong_bfp.cu); false when the fine level is not

@@ -2,12 +2,16 @@
 // its rms and <N>) with the stencil staged once per block in shared memory
 // as block fixed-point integers (bfp.cuh), for levels whose colour rows are a
 // multiple of 32 long:
-//   RR = true:  the fused residual and FAS restriction (R u, R d of the 8
-//               children of every coarse cell, Eq. general_pde_numerical_coarse),
-//   RR = false: the residual norm only, optionally writing -d as FP32 (the
-//               FP64 defect of the mixed-precision solve).
-// Both reduce (sum N, sum d, sum d^2, square-root clamps) over the grid in a
-// fixed order (deterministic).  Per fine cell: S6 - 6u exact in 64-bit
+//   MODE 1 (restriction): the fused residual and FAS restriction (R u, R d of
+//               the 8 children of every coarse cell, Eq.
+//               general_pde_numerical_coarse), reducing sum N and the clamps,
+//   MODE 0 (norm): the residual norm, optionally writing -d as FP32 (the
+//               FP64 defect of the mixed-precision solve), reducing sum N,
+//               sum d, sum d^2 and the clamps,
+//   MODE 2 (coarse source): on the coarse level, the FAS right-hand side
+//               f = L(R u) - (R d + dc) written in place over R d, reducing
+//               sum N (the coarse level's first compatibility constant).
+// Every reduction runs over the grid in a fixed order (deterministic).  Per fine cell: S6 - 6u exact in 64-bit
 // integers and Q16 exact in 128 bits, each rounded once (as fixsum.cuh), N
 // from the FP32 estimate with one FP64 Newton step (dgp64_N_nt) or the
 // rationalised FP64 form where that is not safe; d = (S6 - 6u)/h^2 - N - f
@@ -32,17 +36,19 @@ constexpr int RR_TJ = 8;   // tile rows: a warp covers 16 columns of two rows
 
 }
 
-// HASF: the level has a FAS source f (every level but the finest); MODEL:
-// 0 nDGP, 1 Kmouflage
-template <bool RR, bool HASF, int MODEL>
+// MODE: above; HASF: the level has a FAS source f (every level but the
+// finest; in MODE 2 f is R d, read and overwritten through FW0, FW1, and the
+// shift is -dc of the fine level, scf); MODEL: 0 nDGP, 1 Kmouflage
+template <int MODE, bool HASF, int MODEL>
 __global__ void __launch_bounds__(bfp::THREADS, 3)
 k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const double *__restrict__ S0,
             const double *__restrict__ S1, const double *__restrict__ F0, const double *__restrict__ F1, LevScal *sc,
             RedBuf rb, LevK<double> L, const OpK<double> *__restrict__ opp, double *__restrict__ Uc0,
             double *__restrict__ Uc1, double *__restrict__ URc0, double *__restrict__ URc1,
             double *__restrict__ RDc0, double *__restrict__ RDc1, float *__restrict__ D0, float *__restrict__ D1,
-            DgpK64 dk, int zc)
+            double *FW0, double *FW1, const LevScal *__restrict__ scf, DgpK64 dk, int zc)
 {
+    constexpr bool RR = MODE == 1, CS = MODE == 2;
     __shared__ bfp::Shared<RR_TJ> t;
     __shared__ double s_c[2];
     __shared__ NtK s_nk;
@@ -54,7 +60,7 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
     const int i0 = blockIdx.z * zc, i1 = min(n, i0 + zc);
     if (tid == 0) {
         s_c[0] = sc->c;
-        s_c[1] = sc->c - sc->fshift;
+        s_c[1] = CS ? -scf->dc : sc->c - sc->fshift;
         s_nk = make_ntk(*opp, dk);
     }
     // ring colour slots: 0 = the colour-0 array, 1 = the colour-1 array
@@ -74,15 +80,18 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
     bool kok;
     long long kv = bfp::fold(kc, g.ef, kok);
     const long long rowo = (long long)j * half + m;
-    // the cells' s and f are read a plane ahead, like the staged planes
+    // the cells' s and f are read a plane ahead, like the staged planes (f
+    // by plain loads where this pass overwrites it: each thread reads its
+    // cells' f before it writes them)
+    auto ldf = [&](int c, long long r) { return CS ? (c ? FW1 : FW0)[r] : __ldg((c ? F1 : F0) + r); };
     double s_nx[2], f_nx[2] = {0.0, 0.0};
     {
         const long long r0 = (long long)i0 * g.pstride + rowo;
         s_nx[0] = __ldg(S0 + r0);
         s_nx[1] = __ldg(S1 + r0);
         if (HASF) {
-            f_nx[0] = __ldg(F0 + r0);
-            f_nx[1] = __ldg(F1 + r0);
+            f_nx[0] = ldf(0, r0);
+            f_nx[1] = ldf(1, r0);
         }
     }
     for (int i = i0, step = 0; i < i1; ++i, ++step) {
@@ -94,8 +103,8 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
             s_nx[0] = __ldg(S0 + rowi + g.pstride);
             s_nx[1] = __ldg(S1 + rowi + g.pstride);
             if (HASF) {
-                f_nx[0] = __ldg(F0 + rowi + g.pstride);
-                f_nx[1] = __ldg(F1 + rowi + g.pstride);
+                f_nx[0] = ldf(0, rowi + g.pstride);
+                f_nx[1] = ldf(1, rowi + g.pstride);
             }
         }
         const bool fx = fx_ok(g.ef);
@@ -108,7 +117,6 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
         for (int c = 0; c < 2; ++c) {
             const int p = (c + i + j) & 1;
             const double s = sv[c];
-            const double *F = c ? F1 : F0;
             double N, d;
             int cl = 0;
             if (fx) {
@@ -133,7 +141,9 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
                 const double u = __ldg((c ? U1 : U0) + rowi);
                 if (RR) su += u;
                 if (MODEL == 0) {
-                    d = dgp64_resid(op, dk, nk, v, u, s, HASF ? F + rowi : nullptr, cshift, L.inv_h2, N, cl);
+                    d = dgp64_resid(op, dk, nk, v, u, s, (HASF && !CS) ? (c ? F1 : F0) + rowi : nullptr, cshift,
+                                    L.inv_h2, N, cl);
+                    if (CS) d -= fv[c];
                 } else {
                     N = op_N<double, 1>(op, L, v, s, cl);
                     const double S6 = (v.xp + v.xm) + (v.yp + v.ym) + (v.zp + v.zm);
@@ -145,6 +155,8 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
             nclamp += cl;
             if (RR) {
                 sd += d;
+            } else if (CS) {
+                (c ? FW1 : FW0)[rowi] = d;
             } else {
                 acc[1] += d;
                 acc[2] = fma(d, d, acc[2]);
@@ -184,12 +196,18 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
     if (grid_sum<4>(acc, rb, tot) && tid == 0) {
         const double cnt = (double)n * n * n;
         const double c_new = tot[0] / cnt;
-        const double dc = c_new - c_old;
-        set_c(sc, c_new);
-        sc->dc = dc;
-        // (the restriction pass sums neither d nor d^2: its residual norm is
-        // not used, and the norm pass gives it where it is)
-        sc->eps2 = RR ? __longlong_as_double(0x7FF8000000000000LL) : (tot[2] + 2.0 * dc * tot[1] + cnt * dc * dc) / cnt;
+        if (CS) {
+            set_c_fshift(sc, c_new, c_new);
+            sc->dc = 0.0;
+        } else {
+            const double dc = c_new - c_old;
+            set_c(sc, c_new);
+            sc->dc = dc;
+            // (the restriction pass sums neither d nor d^2: its residual norm
+            // is not used, and the norm pass gives it where it is)
+            sc->eps2 = RR ? __longlong_as_double(0x7FF8000000000000LL)
+                          : (tot[2] + 2.0 * dc * tot[1] + cnt * dc * dc) / cnt;
+        }
         sc->sumN = tot[0];
         sc->clamps = tot[3];
     }
@@ -220,10 +238,10 @@ bool launch_resid_restrict_bfp(const LevArrays<double> &Lf, LevArrays<double> &L
     const dim3 g(Lf.half / bfp::TM, Lf.n / RR_TJ, (Lf.n + zc - 1) / zc);
     if ((long long)g.x * g.y * g.z > rb.cap) return false;
 #define MG_RRB(HASF, MODEL)                                                                                  \
-    k_resid_bfp<true, HASF, MODEL><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb,   \
+    k_resid_bfp<1, HASF, MODEL><<<g, b, 0, st>>>(Lf.U(0), Lf.U(1), Lf.s[0], Lf.s[1], Lf.f[0], Lf.f[1], Lf.sc, rb,      \
                                              make_levk<double>(Lf.n, Lf.h), op, Lc.U(0), Lc.U(1), Lc.ur[0],      \
-                                             Lc.ur[1], Lc.fbuf[0], Lc.fbuf[1], nullptr, nullptr,                \
-                                             make_dgpk64(Lf.h), zc)
+                                             Lc.ur[1], Lc.fbuf[0], Lc.fbuf[1], nullptr, nullptr, nullptr,       \
+                                             nullptr, nullptr, make_dgpk64(Lf.h), zc)
     if (Lf.model == 0) {
         if (Lf.f[0]) MG_RRB(true, 0);
         else MG_RRB(false, 0);
@@ -244,10 +262,10 @@ bool launch_resid_norm_bfp(const LevArrays<double> &L, const OpK<double> *op, co
     const dim3 g(L.half / bfp::TM, L.n / RR_TJ, (L.n + zc - 1) / zc);
     if ((long long)g.x * g.y * g.z > rb.cap) return false;
 #define MG_RNB(HASF, MODEL)                                                                                   \
-    k_resid_bfp<false, HASF, MODEL><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb,           \
+    k_resid_bfp<0, HASF, MODEL><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb,           \
                                               make_levk<double>(L.n, L.h), op, nullptr, nullptr, nullptr, nullptr, \
-                                              nullptr, nullptr, D ? D[0] : nullptr, D ? D[1] : nullptr,           \
-                                              make_dgpk64(L.h), zc)
+                                              nullptr, nullptr, D ? D[0] : nullptr, D ? D[1] : nullptr, nullptr,  \
+                                              nullptr, nullptr, make_dgpk64(L.h), zc)
     if (L.model == 0) {
         if (L.f[0]) MG_RNB(true, 0);
         else MG_RNB(false, 0);
@@ -256,6 +274,28 @@ bool launch_resid_norm_bfp(const LevArrays<double> &L, const OpK<double> *op, co
         else MG_RNB(false, 1);
     }
 #undef MG_RNB
+    return true;
+}
+
+// the coarse level's FAS source f = L(R u) - (R d + dc) over R d in place
+// (R u in Lc.ur, R d in Lc.fbuf, dc from the fine level's scalars); false
+// when the coarse level is not eligible
+bool launch_coarse_source_bfp(const LevArrays<double> &Lf, const LevArrays<double> &Lc, const OpK<double> *op,
+                              const RedBuf &rb, cudaStream_t st)
+{
+    if (!bfp_eligible(Lc)) return false;
+    const int zc = bfp_planes(Lc, rb.cap);
+    const dim3 b(bfp::THREADS, 1, 1);
+    const dim3 g(Lc.half / bfp::TM, Lc.n / RR_TJ, (Lc.n + zc - 1) / zc);
+    if ((long long)g.x * g.y * g.z > rb.cap) return false;
+#define MG_CSB(MODEL)                                                                                         \
+    k_resid_bfp<2, true, MODEL><<<g, b, 0, st>>>(Lc.ur[0], Lc.ur[1], Lc.s[0], Lc.s[1], nullptr, nullptr, Lc.sc, rb,  \
+                                                 make_levk<double>(Lc.n, Lc.h), op, nullptr, nullptr, nullptr,    \
+                                                 nullptr, nullptr, nullptr, nullptr, nullptr, Lc.fbuf[0],        \
+                                                 Lc.fbuf[1], Lf.sc, make_dgpk64(Lc.h), zc)
+    if (Lc.model == 0) MG_CSB(0);
+    else MG_CSB(1);
+#undef MG_CSB
     return true;
 }
 

@@ -105,6 +105,22 @@ def test_coarse_source(B, ctx, name, prec):
     assert abs(cg - cH) <= TOL[prec] * scale
 
 
+@pytest.mark.parametrize("name", list(MODELS))
+@pytest.mark.parametrize("n", [128, 256])
+def test_coarse_source_staged(B, ctx, name, n):
+    # coarse levels of 128^3 and more take the block-staged FP64 kernel
+    o, b, amp = ops(B, name)
+    h = 2.0
+    Ru, s, Rd = fields(n, 31, amp)
+    LH, cH, _ = oracle.residual(o, Ru, s, None, h)
+    ref = LH - Rd
+    out = np.empty_like(Ru)
+    cg = B.mg_op_coarse_source(ctx, b, 0, n, h, Ru, Rd, s, out)
+    scale = np.abs(LH).max() + 12.0 * np.abs(Ru).max() / h ** 2 + np.abs(Rd).max()
+    assert np.abs(out - ref).max() < TOL[0] * scale
+    assert abs(cg - cH) <= TOL[0] * scale
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n", [8, 16, 24])
 def test_prolongation(B, ctx, prec, n):
