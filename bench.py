@@ -51,7 +51,7 @@ FLOPS_PER_CELL_FP64 = 41
 # issues per SM per clock: ALU and the FMA pipe's integer half 4
 # sub-partitions x 16 lanes, all instructions 4 x 32; the FP64 rate comes
 # from the probe at run time
-FP64_MIX = {"fp64": 5.0, "alu": 260.0, "fma": 154.0, "issue": 540.0}
+FP64_MIX = {"fp64": 5.0, "alu": 259.0, "fma": 122.0, "issue": 522.0}
 PIPE_RATE = {"alu": 64.0, "fma": 64.0, "issue": 128.0}
 
 
@@ -438,7 +438,7 @@ def main():
     # with the mesh they were measured on (profiles/k_smooth_bfp_fp64_ndgp_256.md
     # and profiles/k_smooth4_fp32corr_ndgp_512.md, both at 512^3), scaled by
     # the cell count to this mesh
-    TRAFFIC = {"fp64": (1672.3e6 + 516.1e6, 512), "mixed": (1670.8e6 + 255.4e6, 512)}
+    TRAFFIC = {"fp64": (1675.9e6 + 516.1e6, 512), "mixed": (1670.8e6 + 255.4e6, 512)}
 
     def roofline(r, precision, fp64_tf):
         """Roofline of the finest half-sweep, anchored to the HBM peak (the
