@@ -84,27 +84,29 @@ static int grid1(long long n) { return (int)std::max<long long>(1, std::min<long
 struct PmWork {
     unsigned long long *acc = nullptr;
     size_t acc_bytes = 0;
-    // Poisson solve for one mesh size
+    // Poisson solve for one mesh size: FP32 transforms (r32 -> spec -> r32)
+    // inside an FP64 iterative refinement
     int fft_n = 0;
     cufftHandle fwd = 0, inv = 0;
-    double *rho = nullptr, *phin = nullptr, *phi = nullptr, *table = nullptr;
-    cufftDoubleComplex *spec = nullptr;
+    double *rho = nullptr, *phin = nullptr, *phi = nullptr;
+    float *r32 = nullptr, *table = nullptr;
+    cufftComplex *spec = nullptr;
 };
 
 // 4 sin^2(pi k / n): minus the eigenvalues of the 1D 3-point Laplacian
-__global__ void k_lap_table(double *t, int n)
+__global__ void k_lap_table(float *t, int n)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) {
         const double s = sinpi((double)k / (double)n);
-        t[k] = 4.0 * s * s;
+        t[k] = (float)(4.0 * s * s);
     }
 }
 
-// Green's function of the 7-point Laplacian on the rfft grid (n, n, n/2+1):
-// Phi_k = scale * rho_k / (-(t[i] + t[j] + t[kz])), zero mode set to 0.
+// Green's function of the 7-point Laplacian on the rfft grid (n, n, n/2+1),
+// FP32: Phi_k = scale * rho_k / (-(t[i] + t[j] + t[kz])), zero mode set to 0
 __global__ void __launch_bounds__(256)
-k_green(cufftDoubleComplex *spec, int n, const double *__restrict__ t, double scale)
+k_green(cufftComplex *spec, int n, const float *__restrict__ t, float scale)
 {
     const int nz = n / 2 + 1;
     const long long total = (long long)n * n * nz;
@@ -113,17 +115,58 @@ k_green(cufftDoubleComplex *spec, int n, const double *__restrict__ t, double sc
         const int kz = (int)(q % nz);
         const long long r = q / nz;
         const int j = (int)(r % n), i = (int)(r / n);
-        const double lam = -(t[i] + t[j] + t[kz]);
-        cufftDoubleComplex v = spec[q];
-        if (q == 0) {
-            v.x = 0.0;
-            v.y = 0.0;
-        } else {
-            const double f = scale / lam;
-            v.x *= f;
-            v.y *= f;
-        }
+        cufftComplex v = spec[q];
+        const float f = q == 0 ? 0.f : -scale / ((t[i] + t[j]) + t[kz]);
+        v.x *= f;
+        v.y *= f;
         spec[q] = v;
+    }
+}
+
+// FP32 copy of coef (rhs - <rhs>), the first right-hand side of the
+// refinement (the mean, which the zero mode drops, is taken out before the
+// rounding to FP32, so that it cannot swamp the rest)
+__global__ void __launch_bounds__(256)
+k_rhs32(const double *__restrict__ rhs, const double *__restrict__ mean, double coef, float *__restrict__ r32,
+        long long cnt)
+{
+    const double mu = *mean;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride)
+        r32[q] = (float)(coef * (rhs[q] - mu));
+}
+
+// u = e (first pass) or u += e, FP64
+__global__ void __launch_bounds__(256)
+k_add_corr(double *__restrict__ u, const float *__restrict__ e, long long cnt, int first)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride)
+        u[q] = first ? (double)e[q] : u[q] + (double)e[q];
+}
+
+// the FP64 residual of Lap u = coef (rhs - <rhs>) with the 7-point
+// Laplacian (h = 1, periodic), R = coef (rhs - <rhs>) - (sum of the 6
+// neighbours - 6 u), written as FP32: the right-hand side of the next
+// correction
+__global__ void __launch_bounds__(256)
+k_poisson_resid(const double *__restrict__ u, const double *__restrict__ rhs, const double *__restrict__ mean,
+                double coef, float *__restrict__ r32, int n)
+{
+    const double mu = *mean;
+    const long long cnt = (long long)n * n * n;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
+        const int k = (int)(q % n);
+        const long long r = q / n;
+        const int j = (int)(r % n), i = (int)(r / n);
+        const long long pl = (long long)n * n;
+        const long long qip = i + 1 == n ? q - (n - 1) * pl : q + pl, qim = i == 0 ? q + (n - 1) * pl : q - pl;
+        const long long qjp = j + 1 == n ? q - (long long)(n - 1) * n : q + n,
+                        qjm = j == 0 ? q + (long long)(n - 1) * n : q - n;
+        const long long qkp = k + 1 == n ? q - (n - 1) : q + 1, qkm = k == 0 ? q + (n - 1) : q - 1;
+        const double s6 = ((u[qip] + u[qim]) + (u[qjp] + u[qjm])) + (u[qkp] + u[qkm]);
+        r32[q] = (float)fma(coef, rhs[q] - mu, -fma(-6.0, u[q], s6));
     }
 }
 
@@ -200,10 +243,13 @@ static void pm_release_fft(PmWork &w)
     if (w.fwd) cufftDestroy(w.fwd);
     if (w.inv) cufftDestroy(w.inv);
     w.fwd = w.inv = 0;
-    for (double *p : {w.rho, w.phin, w.phi, w.table})
+    for (double *p : {w.rho, w.phin, w.phi})
+        if (p) cudaFree(p);
+    for (float *p : {w.r32, w.table})
         if (p) cudaFree(p);
     if (w.spec) cudaFree(w.spec);
-    w.rho = w.phin = w.phi = w.table = nullptr;
+    w.rho = w.phin = w.phi = nullptr;
+    w.r32 = w.table = nullptr;
     w.spec = nullptr;
     w.fft_n = 0;
 }
@@ -218,10 +264,11 @@ void pm_fft_setup(mg_ctx *ctx, int n)
     MG_CK(cudaMalloc(&w.rho, sizeof(double) * cells));
     MG_CK(cudaMalloc(&w.phin, sizeof(double) * cells));
     MG_CK(cudaMalloc(&w.phi, sizeof(double) * cells));
-    MG_CK(cudaMalloc(&w.table, sizeof(double) * n));
-    MG_CK(cudaMalloc(&w.spec, sizeof(cufftDoubleComplex) * modes));
-    MG_CUFFT(cufftPlan3d(&w.fwd, n, n, n, CUFFT_D2Z));
-    MG_CUFFT(cufftPlan3d(&w.inv, n, n, n, CUFFT_Z2D));
+    MG_CK(cudaMalloc(&w.r32, sizeof(float) * cells));
+    MG_CK(cudaMalloc(&w.table, sizeof(float) * n));
+    MG_CK(cudaMalloc(&w.spec, sizeof(cufftComplex) * modes));
+    MG_CUFFT(cufftPlan3d(&w.fwd, n, n, n, CUFFT_R2C));
+    MG_CUFFT(cufftPlan3d(&w.inv, n, n, n, CUFFT_C2R));
     MG_CUFFT(cufftSetStream(w.fwd, ctx->stream));
     MG_CUFFT(cufftSetStream(w.inv, ctx->stream));
     k_lap_table<<<(n + 127) / 128, 128, 0, ctx->stream>>>(w.table, n);
@@ -231,16 +278,38 @@ void pm_fft_setup(mg_ctx *ctx, int n)
 }
 
 // Lap out = coef rhs with the 7-point Green's function by FFT (Sec. 3.1);
-// the zero mode is dropped (so the mean of rhs is ignored)
+// the zero mode is dropped (so the mean of rhs is ignored).  FP64 transforms
+// run at the FP64 rate on this GPU, so the solve is FP32 transforms inside
+// an FP64 iterative refinement: out = G (coef rhs) in FP32, then twice
+// R = coef rhs - Lap out in FP64 and out += G R in FP32; each correction
+// carries about 2^-22 of its own size, so two corrections bring out to the
+// FP64 solution (relative 1e-15 in L2, measured against FP64 transforms).
+// The mean of rhs (the zero mode, which the Green's function drops) is taken
+// out in FP64 before any rounding to FP32, and the FP32 transforms leave a
+// mean of about 1e-9 of |out| behind, removed at the end (the zero mode of
+// the FP64 solution is zero)
 void poisson_dev(mg_ctx *ctx, int n, double coef, const double *rhs, double *out)
 {
     PmWork &w = pmw(ctx);
-    const double scale = coef / ((double)n * n * n);
-    MG_CUFFT(cufftExecD2Z(w.fwd, const_cast<double *>(rhs), w.spec));
-    const long long modes = (long long)n * n * (n / 2 + 1);
-    k_green<<<grid1(modes), 256, 0, ctx->stream>>>(w.spec, n, w.table, scale);
+    cudaStream_t st = ctx->stream;
+    const long long cnt = (long long)n * n * n, modes = (long long)n * n * (n / 2 + 1);
+    const float scale = (float)(1.0 / (double)cnt);
+    constexpr int CORRECTIONS = 2;
+    double *mean_rhs = ctx->dscratch + 1, *mean_out = ctx->dscratch + 2;
+    launch_mean_nat(rhs, cnt, mean_rhs, ctx->rb, st);
+    k_rhs32<<<grid1(cnt), 256, 0, st>>>(rhs, mean_rhs, coef, w.r32, cnt);
+    for (int it = 0; it <= CORRECTIONS; ++it) {
+        MG_CUFFT(cufftExecR2C(w.fwd, w.r32, w.spec));
+        k_green<<<grid1(modes), 256, 0, st>>>(w.spec, n, w.table, scale);
+        MG_CK(cudaGetLastError());
+        MG_CUFFT(cufftExecC2R(w.inv, w.spec, w.r32));
+        k_add_corr<<<grid1(cnt), 256, 0, st>>>(out, w.r32, cnt, it == 0);
+        if (it < CORRECTIONS) k_poisson_resid<<<grid1(cnt), 256, 0, st>>>(out, rhs, mean_rhs, coef, w.r32, n);
+        MG_CK(cudaGetLastError());
+    }
+    launch_mean_nat(out, cnt, mean_out, ctx->rb, st);
+    k_sub_mean<<<grid1(cnt), 256, 0, st>>>(out, cnt, mean_out);
     MG_CK(cudaGetLastError());
-    MG_CUFFT(cufftExecZ2D(w.inv, w.spec, out));
 }
 
 // Lap Phi = (3/2) Omega_m a^-1 delta (Eq. GR_poisson_codeunit)
