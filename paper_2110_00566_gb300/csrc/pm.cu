@@ -89,6 +89,7 @@ struct PmWork {
     int fft_n = 0;
     cufftHandle fwd = 0, inv = 0;
     double *rho = nullptr, *phin = nullptr, *phi = nullptr;
+    double *pot = nullptr, *g3 = nullptr;   // the force's potential and -grad of it (3 components)
     float *r32 = nullptr, *table = nullptr;
     cufftComplex *spec = nullptr;
 };
@@ -170,13 +171,8 @@ k_poisson_resid(const double *__restrict__ u, const double *__restrict__ rhs, co
     }
 }
 
-// -grad Phi by 3-point differences at the 8 CIC cells, interpolated with the
-// CIC weights, then the leapfrog kick and drift (code units of Sec. 3.1.1):
-//   p = p fr + g ck,  x += p cd,  wrap into [0, ng).  Phi = PhiN + cphi phi
-// when phi is given (nDGP: cphi = 1/2, Eq. poisson_nDGP; Kmouflage: cphi =
-// beta c~, Eq. force_Kmo2, whose friction term gives fr = 1 - beta
-// (dphibar/da) da_kick; fr = 1 otherwise).  Rounded as written (no
-// contraction).
+// the potential of the force at cell q: A + cb Bp (Bp given), rounded as
+// written (no contraction)
 __device__ __forceinline__ double pot(const double *__restrict__ A, const double *__restrict__ Bp, double cb,
                                       long long q)
 {
@@ -184,9 +180,51 @@ __device__ __forceinline__ double pot(const double *__restrict__ A, const double
     return Bp ? __dadd_rn(a, __dmul_rn(cb, __ldg(Bp + q))) : a;
 }
 
+// the potential Phi = PhiN + cphi phi (phi given) on the mesh, rounded as
+// the per-corner evaluation of the force would round it
 __global__ void __launch_bounds__(256)
-k_kick_drift(float *__restrict__ pos, float *__restrict__ mom, long long np, int ng, const double *__restrict__ phin,
-             const double *__restrict__ phi, double cphi, double fr, double ck, double cd)
+k_pot(const double *__restrict__ phin, const double *__restrict__ phi, double cphi, double *__restrict__ out,
+      long long cnt)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride)
+        out[q] = pot(phin, phi, cphi, q);
+}
+
+// -grad Phi by 3-point differences on the mesh, g_c = -(Phi(+e_c) -
+// Phi(-e_c)) / 2 (the arithmetic of the per-corner force, so that the
+// interpolated force is bit-identical to evaluating it at the corners)
+__global__ void __launch_bounds__(256)
+k_force_mesh(const double *__restrict__ P, double *__restrict__ gx, double *__restrict__ gy, double *__restrict__ gz,
+             int n)
+{
+    const long long cnt = (long long)n * n * n, pl = (long long)n * n;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
+        const int k = (int)(q % n);
+        const long long r = q / n;
+        const int j = (int)(r % n), i = (int)(r / n);
+        const long long qip = i + 1 == n ? q - (n - 1) * pl : q + pl, qim = i == 0 ? q + (n - 1) * pl : q - pl;
+        const long long qjp = j + 1 == n ? q - (long long)(n - 1) * n : q + n,
+                        qjm = j == 0 ? q + (long long)(n - 1) * n : q - n;
+        const long long qkp = k + 1 == n ? q - (n - 1) : q + 1, qkm = k == 0 ? q + (n - 1) : q - 1;
+        gx[q] = -__dsub_rn(__ldg(P + qip), __ldg(P + qim)) / 2.0;
+        gy[q] = -__dsub_rn(__ldg(P + qjp), __ldg(P + qjm)) / 2.0;
+        gz[q] = -__dsub_rn(__ldg(P + qkp), __ldg(P + qkm)) / 2.0;
+    }
+}
+
+// the force at each particle interpolated from the mesh force with the CIC
+// weights, then the leapfrog kick and drift (code units of Sec. 3.1.1):
+//   p = p fr + g ck,  x += p cd,  wrap into [0, ng).  Phi = PhiN + cphi phi
+// when phi is given (nDGP: cphi = 1/2, Eq. poisson_nDGP; Kmouflage: cphi =
+// beta c~, Eq. force_Kmo2, whose friction term gives fr = 1 - beta
+// (dphibar/da) da_kick; fr = 1 otherwise).  Rounded as written (no
+// contraction); the weight of corner (a, b, c) is (w_a w_b) w_c, with w_a w_b
+// formed once per (a, b)
+__global__ void __launch_bounds__(256)
+k_kick_drift(float *__restrict__ pos, float *__restrict__ mom, long long np, int ng, const double *__restrict__ gx,
+             const double *__restrict__ gy, const double *__restrict__ gz, double fr, double ck, double cd)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np; p += stride) {
@@ -195,22 +233,21 @@ k_kick_drift(float *__restrict__ pos, float *__restrict__ mom, long long np, int
 #pragma unroll
         for (int d = 0; d < 3; ++d) cic_axis(pos[3 * p + d], ng, i0[d], i1[d], w0[d], w1[d]);
         double g[3] = {0.0, 0.0, 0.0};
+#pragma unroll
         for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const double wab = __dmul_rn(a ? w1[0] : w0[0], b ? w1[1] : w0[1]);
+                const long long rab = ((long long)(a ? i1[0] : i0[0]) * ng + (b ? i1[1] : i0[1])) * ng;
+#pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    const double w = __dmul_rn(__dmul_rn(a ? w1[0] : w0[0], b ? w1[1] : w0[1]), c ? w1[2] : w0[2]);
-                    const int i = a ? i1[0] : i0[0], j = b ? i1[1] : i0[1], k = c ? i1[2] : i0[2];
-                    const int ip = i + 1 == ng ? 0 : i + 1, im = i == 0 ? ng - 1 : i - 1;
-                    const int jp = j + 1 == ng ? 0 : j + 1, jm = j == 0 ? ng - 1 : j - 1;
-                    const int kp = k + 1 == ng ? 0 : k + 1, km = k == 0 ? ng - 1 : k - 1;
-                    auto I3 = [ng](int x, int y, int z) { return ((long long)x * ng + y) * ng + z; };
-                    const double gx = -__dsub_rn(pot(phin, phi, cphi, I3(ip, j, k)), pot(phin, phi, cphi, I3(im, j, k))) / 2.0;
-                    const double gy = -__dsub_rn(pot(phin, phi, cphi, I3(i, jp, k)), pot(phin, phi, cphi, I3(i, jm, k))) / 2.0;
-                    const double gz = -__dsub_rn(pot(phin, phi, cphi, I3(i, j, kp)), pot(phin, phi, cphi, I3(i, j, km))) / 2.0;
-                    g[0] = __dadd_rn(g[0], __dmul_rn(w, gx));
-                    g[1] = __dadd_rn(g[1], __dmul_rn(w, gy));
-                    g[2] = __dadd_rn(g[2], __dmul_rn(w, gz));
+                    const double w = __dmul_rn(wab, c ? w1[2] : w0[2]);
+                    const long long q = rab + (c ? i1[2] : i0[2]);
+                    g[0] = __dadd_rn(g[0], __dmul_rn(w, __ldg(gx + q)));
+                    g[1] = __dadd_rn(g[1], __dmul_rn(w, __ldg(gy + q)));
+                    g[2] = __dadd_rn(g[2], __dmul_rn(w, __ldg(gz + q)));
                 }
+            }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const float pn = (float)__dadd_rn(__dmul_rn((double)mom[3 * p + d], fr), __dmul_rn(g[d], ck));
@@ -243,12 +280,12 @@ static void pm_release_fft(PmWork &w)
     if (w.fwd) cufftDestroy(w.fwd);
     if (w.inv) cufftDestroy(w.inv);
     w.fwd = w.inv = 0;
-    for (double *p : {w.rho, w.phin, w.phi})
+    for (double *p : {w.rho, w.phin, w.phi, w.pot, w.g3})
         if (p) cudaFree(p);
     for (float *p : {w.r32, w.table})
         if (p) cudaFree(p);
     if (w.spec) cudaFree(w.spec);
-    w.rho = w.phin = w.phi = nullptr;
+    w.rho = w.phin = w.phi = w.pot = w.g3 = nullptr;
     w.r32 = w.table = nullptr;
     w.spec = nullptr;
     w.fft_n = 0;
@@ -264,6 +301,8 @@ void pm_fft_setup(mg_ctx *ctx, int n)
     MG_CK(cudaMalloc(&w.rho, sizeof(double) * cells));
     MG_CK(cudaMalloc(&w.phin, sizeof(double) * cells));
     MG_CK(cudaMalloc(&w.phi, sizeof(double) * cells));
+    MG_CK(cudaMalloc(&w.pot, sizeof(double) * cells));
+    MG_CK(cudaMalloc(&w.g3, sizeof(double) * 3 * cells));
     MG_CK(cudaMalloc(&w.r32, sizeof(float) * cells));
     MG_CK(cudaMalloc(&w.table, sizeof(float) * n));
     MG_CK(cudaMalloc(&w.spec, sizeof(cufftComplex) * modes));
@@ -516,7 +555,15 @@ int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats)
         const bool own_e = st->e_a > 0.0 && st->e_mid > 0.0;   // the caller's expansion history
         const double ck = dak / (a * (own_e ? st->e_a : E_lcdm(a, om)));
         const double cd = da / (std::pow(am, 3.0) * (own_e ? st->e_mid : E_lcdm(am, om)));
-        k_kick_drift<<<grid1(st->np), 256, 0, ctx->stream>>>(dpos, dmom, st->np, n, w.phin, dphi, cphi, fr, ck, cd);
+        const long long cells = (long long)n * n * n;
+        const double *P = w.phin;
+        if (dphi) {
+            k_pot<<<grid1(cells), 256, 0, ctx->stream>>>(w.phin, dphi, cphi, w.pot, cells);
+            P = w.pot;
+        }
+        k_force_mesh<<<grid1(cells), 256, 0, ctx->stream>>>(P, w.g3, w.g3 + cells, w.g3 + 2 * cells, n);
+        k_kick_drift<<<grid1(st->np), 256, 0, ctx->stream>>>(dpos, dmom, st->np, n, w.g3, w.g3 + cells,
+                                                             w.g3 + 2 * cells, fr, ck, cd);
         MG_CK(cudaGetLastError());
         stage_out(ctx, st->pos, dpos, pb);
         stage_out(ctx, st->mom, dmom, pb);
