@@ -285,29 +285,50 @@ __device__ __forceinline__ Diffs diffs(const long long *Sm, const long long *S0,
 
 // N_K of the Kmouflage operator (Sec. 3.2.4, Eq. kmf_eqn_codeunit_final
 // over c~) from the staged integers: the linear parts -- Delta_a, the
-// combinations 2 S_a - S_b - S_c and C_ab -- exact integers rounded once to
-// binary64 at the scale ef, the rest in FP64:
-//   G^2 = sum_a Delta_a^2 / (4 h^2),
-//   T = sum_a Delta_a^2 (2 S_a - S_b - S_c) / (12 h^4) + sum_{a<b} C_ab Delta_a Delta_b / (8 h^4),
+// combinations 2 S_a - S_b - S_c and 1.5 C_ab -- exact integers rounded once
+// to binary64 at the scale ef, the rest in FP64.  With S2 = sum_a Delta_a^2
+// (G^2 = S2 / (4 h^2)) and T' = sum_a Delta_a^2 (2 S_a - S_b - S_c) +
+// (3/2) sum_{a<b} C_ab Delta_a Delta_b (T = T' / (12 h^4): the cross
+// coefficient 1/(8 h^4) is 3/2 of 1/(12 h^4)),
 //   N_K = (s - k3 (G^2)^(n-2) T) / (k1 + k2 (G^2)^(n-1))
-// (k1 = 1 + gamma (phibar'/H0)^(2(n-1)), k2 = (2n+1) gamma / 3,
-// k2 = 2 (n-1) gamma); the quotient by the corrected single-precision
-// reciprocal (k_quot: the denominator is at least 1)
-__device__ __forceinline__ double kmo64_N(const OpK<double> &op, const LevK<double> &L, const Sums &r, const Diffs &d,
+//       = (s - KA S2^(n-2) T') / (k1 + KB S2^(n-1)),
+// KA = k3 g^(n-2) / (12 h^4), KB = k2 g^(n-1), g = 1/(4 h^2) (KmoK, per
+// level), so that no power of the level's constants is formed per cell
+// (k1 = 1 + gamma (phibar'/H0)^(2(n-1)), k2 = (2n+1) gamma / 3, k3 = 2 (n-1)
+// gamma); the quotient by the corrected single-precision reciprocal (k_quot:
+// the denominator is at least 1).  19 FP64 instructions for n = 2.
+struct KmoK {
+    double KA, KB;
+    int nm2;   // n - 2
+};
+__device__ __forceinline__ KmoK make_kmok(const OpK<double> &op, const LevK<double> &L)
+{
+    double g = 1.0;
+    for (int q = 0; q < op.nkmo - 2; ++q) g *= L.g2s;
+    return KmoK{op.k3 * L.td * g, op.k2 * g * L.g2s, op.nkmo - 2};
+}
+__device__ __forceinline__ double kmo64_N(const OpK<double> &op, const KmoK &kk, const Sums &r, const Diffs &d,
                                           double s, int ef)
 {
     const double dx = fx_out(d.dx, ef), dy = fx_out(d.dy, ef), dz = fx_out(d.dz, ef);
     const double px = fx_out(2 * r.X - r.Y - r.Z, ef), py = fx_out(2 * r.Y - r.X - r.Z, ef);
     const double pz = fx_out(2 * r.Z - r.X - r.Y, ef);
-    const double cxy = fx_out(r.cxy, ef), cxz = fx_out(r.cxz, ef), cyz = fx_out(r.cyz, ef);
+    // 1.5 C_ab exactly: 3 C_ab (|.| < 2^63) at half the scale
+    const double cxy = fx_out<7>(3 * r.cxy, ef), cxz = fx_out<7>(3 * r.cxz, ef), cyz = fx_out<7>(3 * r.cyz, ef);
     const double dx2 = dx * dx, dy2 = dy * dy, dz2 = dz * dz;
-    const double G2 = ((dx2 + dy2) + dz2) * L.g2s;
-    const double T1 = fma(dx2, px, fma(dy2, py, dz2 * pz));
-    const double T2 = fma(cxy, dx * dy, fma(cxz, dx * dz, cyz * (dy * dz)));
-    const double Tt = fma(L.td, T1, L.to * T2);
-    const double pw = ipow(G2, op.nkmo - 2);
-    const double B = fma(op.k2 * pw, G2, op.k1);
-    const double A = fma(-op.k3 * pw, Tt, s);
+    const double S2 = (dx2 + dy2) + dz2;
+    double T = fma(dx2, px, fma(dy2, py, dz2 * pz));
+    T = fma(cxy, dx * dy, fma(cxz, dx * dz, fma(cyz, dy * dz, T)));
+    double B, A;
+    if (kk.nm2 == 0) {
+        B = fma(kk.KB, S2, op.k1);
+        A = fma(-kk.KA, T, s);
+    } else {
+        double pw = S2;
+        for (int q = 1; q < kk.nm2; ++q) pw *= S2;
+        B = fma(kk.KB * pw, S2, op.k1);
+        A = fma(-kk.KA * pw, T, s);
+    }
     // (an IEEE quotient where B is beyond the reciprocal estimate's range)
     return __double2hiint(B) < ((1023 + 1000) << 20) ? k_quot(A, B) : A / B;
 }

@@ -69,6 +69,7 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
     const double c_old = s_c[0], cshift = s_c[1];
     const NtK nk = s_nk;
     const OpK<double> &op = *opp;
+    const bfp::KmoK kk = MODEL == 1 ? bfp::make_kmok(op, L) : bfp::KmoK{0.0, 0.0, 0};
     const int j = j0 + jt, m = m0 + mt;
     const int jj = jt + 1, mm = mt + 1;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};   // sum N, sum d, sum d^2, clamps
@@ -128,7 +129,7 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
                     N = dgp64_N_any(op, dk, nk, bfp::quad(r, g.ef), s, cl);
                 } else {
                     const bfp::Diffs dd = bfp::diffs<RR_TJ>(t.v[g.sm], t.v[g.s0], t.v[g.sp], c, jj, mm, p);
-                    N = bfp::kmo64_N(op, L, r, dd, s, g.ef);
+                    N = bfp::kmo64_N(op, kk, r, dd, s, g.ef);
                 }
                 if (FOLD)
                     d = fma(L.inv_h2, fx_out(lap6 + kv, g.ef), -N);

@@ -52,6 +52,7 @@ k_smooth_bfp(const double *__restrict__ Uc, const double *__restrict__ Uo, doubl
     const double cf = s_cf;
     const NtK nk = s_nk;
     const OpK<double> &op = *opp;
+    const bfp::KmoK kk = MODEL == 1 ? bfp::make_kmok(op, L) : bfp::KmoK{0.0, 0.0, 0};
     // where the level has no FAS source, the update's constant -h^2 cf / 6 is
     // folded into the fixed-point S6 / 6 (one FP64 add less per cell)
     const double kc = dk.mh6 * cf;
@@ -94,7 +95,7 @@ k_smooth_bfp(const double *__restrict__ Uc, const double *__restrict__ Uo, doubl
                     N = dgp64_N_any(op, dk, nk, bfp::quad(r, g.ef), sv[h], cl);
                 } else {
                     const bfp::Diffs dd = bfp::diffs<SM_TJ>(t.v[g.sm], t.v[g.s0], t.v[g.sp], 0, jj, mm, p);
-                    N = bfp::kmo64_N(op, L, r, dd, sv[h], g.ef);
+                    N = bfp::kmo64_N(op, kk, r, dd, sv[h], g.ef);
                 }
                 if (HASF)
                     out = fma(dk.mh6, N + fcf, fx_out(s6, g.ef));
