@@ -9,6 +9,7 @@
 #include <cufft.h>
 
 #include "ctx.cuh"
+#include "fixsum.cuh"
 
 namespace mg {
 
@@ -149,7 +150,7 @@ k_add_corr(double *__restrict__ u, const float *__restrict__ e, long long cnt, i
 // the FP64 residual of Lap u = coef (rhs - <rhs>) with the 7-point
 // Laplacian (h = 1, periodic), R = coef (rhs - <rhs>) - (sum of the 6
 // neighbours - 6 u), written as FP32: the right-hand side of the next
-// correction
+// correction; the Laplacian exact in 64-bit integers
 __global__ void __launch_bounds__(256)
 k_poisson_resid(const double *__restrict__ u, const double *__restrict__ rhs, const double *__restrict__ mean,
                 double coef, float *__restrict__ r32, int n)
@@ -166,8 +167,24 @@ k_poisson_resid(const double *__restrict__ u, const double *__restrict__ rhs, co
         const long long qjp = j + 1 == n ? q - (long long)(n - 1) * n : q + n,
                         qjm = j == 0 ? q + (long long)(n - 1) * n : q - n;
         const long long qkp = k + 1 == n ? q - (n - 1) : q + 1, qkm = k == 0 ? q + (n - 1) : q - 1;
-        const double s6 = ((u[qip] + u[qim]) + (u[qjp] + u[qjm])) + (u[qkp] + u[qkm]);
-        r32[q] = (float)fma(coef, rhs[q] - mu, -fma(-6.0, u[q], s6));
+        const double v[7] = {u[q], u[qip], u[qim], u[qjp], u[qjm], u[qkp], u[qkm]};
+        // Lap u = S6 - 6 u exactly on the integer pipes at the scale of the
+        // stencil's largest value (fixsum.cuh: the FP64 pipe is this GPU's
+        // narrowest), rounded once; FP64 outside the fixed-point domain
+        int ef = 0;
+#pragma unroll
+        for (int t = 0; t < 7; ++t) ef = max(ef, fx_ef(v[t]));
+        ef = fx_zero_scale(ef);
+        double lap;
+        if (fx_ok(ef)) {
+            long long S = -6 * fx_in(v[0], ef);
+#pragma unroll
+            for (int t = 1; t < 7; ++t) S += fx_in(v[t], ef);
+            lap = fx_out(S, ef);
+        } else {
+            lap = fma(-6.0, v[0], ((v[1] + v[2]) + (v[3] + v[4])) + (v[5] + v[6]));
+        }
+        r32[q] = (float)fma(coef, rhs[q] - mu, -lap);
     }
 }
 
