@@ -91,7 +91,8 @@ k_adj_coef(const double *__restrict__ phi, const double *__restrict__ s, int n, 
     const double h4 = h * h * h * h, qd = 1.0 / (3.0 * h4), qo = 1.0 / (8.0 * h4);
     const double sg = alpha >= 0 ? 1.0 : -1.0, aa = fabs(alpha);
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
-        const int k = (int)(q % n), j = (int)((q / n) % n), i = (int)(q / ((long long)n * n));
+        int i, j, k;
+        split3(q, n, n, i, j, k);
         double t[6];
         q_terms(phi, n, i, j, k, t);
         const double Q = (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]) * qd + (t[3] * t[3] + t[4] * t[4] + t[5] * t[5]) * qo;
@@ -126,7 +127,8 @@ __global__ void __launch_bounds__(256) k_adj_v(AdjLev L)
     const long long stride = (long long)gridDim.x * blockDim.x;
     const double *K[6] = {L.K[0], L.K[1], L.K[2], L.K[3], L.K[4], L.K[5]};
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
-        const int k = (int)(q % n), j = (int)((q / n) % n), i = (int)(q / ((long long)n * n));
+        int i, j, k;
+        split3(q, n, n, i, j, k);
         const int ip = wrap_p(i, n), im = wrap_m(i, n), jp = wrap_p(j, n), jm = wrap_m(j, n);
         const int kp = wrap_p(k, n), km = wrap_m(k, n);
         double r = 0.0;
@@ -151,7 +153,8 @@ k_adj_smooth(AdjLev L, const double *__restrict__ in, double *__restrict__ out, 
     const double m = *mscal, h2 = L.h * L.h;
     const double *K[6] = {L.K[0], L.K[1], L.K[2], L.K[3], L.K[4], L.K[5]};
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
-        const int k = (int)(q % n), j = (int)((q / n) % n), i = (int)(q / ((long long)n * n));
+        int i, j, k;
+        split3(q, n, n, i, j, k);
         if (((i + j + k) & 1) != colour) {
             out[q] = in[q];
             continue;
@@ -162,6 +165,54 @@ k_adj_smooth(AdjLev L, const double *__restrict__ in, double *__restrict__ out, 
         const double mt = mt_apply(K, in, n, i, j, k);
         out[q] = (S6 - h2 * (L.rhs[q] + mt - m * L.v[q])) * (1.0 / 6.0);
     }
+}
+
+// the coarsest level's sweeps in one block, lambda in shared memory (two
+// buffers of the level's cnt <= ADJ_COARSE_MAX cells): per sweep m =
+// <lambda> (a fixed-order block sum), then the two colour half-sweeps of
+// k_adj_smooth; lambda is read from and written back to lam; *mslot ends
+// with the last sweep's m
+constexpr int ADJ_COARSE_MAX = 2048;
+__global__ void __launch_bounds__(256) k_adj_coarsest(AdjLev L, double *lam, double *mslot, int sweeps)
+{
+    extern __shared__ double sbuf[];
+    __shared__ double red[32];
+    __shared__ double s_m;
+    const int n = L.n, cnt = n * n * n, tid = threadIdx.x, nt = blockDim.x;
+    double *buf[2] = {sbuf, sbuf + cnt};
+    for (int q = tid; q < cnt; q += nt) buf[0][q] = lam[q];
+    const double h2 = L.h * L.h;
+    const double *K[6] = {L.K[0], L.K[1], L.K[2], L.K[3], L.K[4], L.K[5]};
+    int cur = 0;
+    for (int sw = 0; sw < sweeps; ++sw) {
+        __syncthreads();
+        double a[1] = {0.0};
+        for (int q = tid; q < cnt; q += nt) a[0] += buf[cur][q];
+        block_sum<1>(a, red);
+        if (tid == 0) s_m = a[0] / (double)cnt;
+        __syncthreads();
+        const double m = s_m;
+        for (int c = 0; c < 2; ++c) {
+            const double *in = buf[cur];
+            double *out = buf[1 - cur];
+            for (int q = tid; q < cnt; q += nt) {
+                const int k = q % n, j = (q / n) % n, i = q / (n * n);
+                if (((i + j + k) & 1) != c) {
+                    out[q] = in[q];
+                    continue;
+                }
+                const double S6 = in[nidx(wrap_p(i, n), j, k, n)] + in[nidx(wrap_m(i, n), j, k, n)] +
+                                  in[nidx(i, wrap_p(j, n), k, n)] + in[nidx(i, wrap_m(j, n), k, n)] +
+                                  in[nidx(i, j, wrap_p(k, n), n)] + in[nidx(i, j, wrap_m(k, n), n)];
+                const double mt = mt_apply(K, in, n, i, j, k);
+                out[q] = (S6 - h2 * (L.rhs[q] + mt - m * L.v[q])) * (1.0 / 6.0);
+            }
+            __syncthreads();
+            cur ^= 1;
+        }
+    }
+    for (int q = tid; q < cnt; q += nt) lam[q] = buf[cur][q];
+    if (tid == 0 && sweeps > 0) *mslot = s_m;
 }
 
 // res = rhs - J^T lambda with m = *mptr (= <lambda>, or 0 if mptr is
@@ -178,7 +229,8 @@ k_adj_resid(AdjLev L, const double *__restrict__ lam, const double *__restrict__
     const double m = mptr ? *mptr : 0.0;
     double acc[2] = {0.0, 0.0};
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
-        const int k = (int)(q % n), j = (int)((q / n) % n), i = (int)(q / ((long long)n * n));
+        int i, j, k;
+        split3(q, n, n, i, j, k);
         const double S6 = lam[nidx(wrap_p(i, n), j, k, n)] + lam[nidx(wrap_m(i, n), j, k, n)] +
                           lam[nidx(i, wrap_p(j, n), k, n)] + lam[nidx(i, wrap_m(j, n), k, n)] +
                           lam[nidx(i, j, wrap_p(k, n), n)] + lam[nidx(i, j, wrap_m(k, n), n)];
@@ -211,7 +263,8 @@ __global__ void __launch_bounds__(256) k_restrict_nat(const double *__restrict__
     const long long cnt = (long long)nc * nc * nc;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
-        const int K = (int)(q % nc), J = (int)((q / nc) % nc), I = (int)(q / ((long long)nc * nc));
+        int I, J, K;
+        split3(q, nc, nc, I, J, K);
         double a = 0.0;
         for (int d = 0; d < 8; ++d) a += f[nidx(2 * I + (d >> 2), 2 * J + ((d >> 1) & 1), 2 * K + (d & 1), nf)];
         c[q] = a * 0.125;
@@ -224,7 +277,8 @@ __global__ void __launch_bounds__(256) k_prolong_nat(double *f, int nf, const do
     const long long cnt = (long long)nf * nf * nf;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
-        const int k = (int)(q % nf), j = (int)((q / nf) % nf), i = (int)(q / ((long long)nf * nf));
+        int i, j, k;
+        split3(q, nf, nf, i, j, k);
         const int I = i >> 1, J = j >> 1, K = k >> 1;
         const int I2 = (i & 1) ? (I + 1 == nc ? 0 : I + 1) : (I == 0 ? nc - 1 : I - 1);
         const int J2 = (j & 1) ? (J + 1 == nc ? 0 : J + 1) : (J == 0 ? nc - 1 : J - 1);
@@ -331,6 +385,11 @@ static void adj_vcycle(mg_ctx *ctx, AdjWork &w, int l, const mg_opts &o)
     };
     const bool coarsest = l + 1 == (int)w.L.size();
     const int sweeps = coarsest ? o.coarse_sweeps : o.pre;
+    if (coarsest && cnt <= ADJ_COARSE_MAX) {
+        // (2 sweeps per sweep flip A.cur twice: the result stays in A.lam[A.cur])
+        k_adj_coarsest<<<1, 256, 2 * sizeof(double) * cnt, s>>>(A, A.lam[A.cur], mslot, sweeps);
+        return;
+    }
     for (int q = 0; q < sweeps; ++q) {
         k_mean_into<<<g1(cnt), 256, 0, s>>>(A.lam[A.cur], cnt, mslot, w.rb);
         sweep();

@@ -33,6 +33,25 @@ struct LevScal {
     float pad_;
 };
 
+// (i, j, k) of the natural-layout index q = (i n + j) nz + k on an
+// n x n x nz mesh, by 32-bit unsigned divisions where q fits (this GPU has
+// no 64-bit integer divider: a 64-bit division or remainder is a long
+// instruction sequence)
+__device__ __forceinline__ void split3(long long q, int n, int nz, int &i, int &j, int &k)
+{
+    if (q < 4294967296LL) {
+        const unsigned u = (unsigned)q, r = u / (unsigned)nz, a = r / (unsigned)n;
+        k = (int)(u - r * (unsigned)nz);
+        j = (int)(r - a * (unsigned)n);
+        i = (int)a;
+    } else {
+        const long long r = q / nz;
+        k = (int)(q - r * nz);
+        j = (int)(r % n);
+        i = (int)(r / n);
+    }
+}
+
 // update c (and the FP32 copy of fshift - c) from a finalising thread
 __device__ __forceinline__ void set_c(LevScal *sc, double c)
 {

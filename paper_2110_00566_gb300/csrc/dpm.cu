@@ -59,9 +59,9 @@ k_ic_spec(const cufftDoubleComplex *__restrict__ in, cufftDoubleComplex *__restr
     const long long total = (long long)n * n * nz;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += stride) {
-        const int kz = (int)(q % nz);
-        const long long r = q / nz;
-        const int mj = freq((int)(r % n), n), mi = freq((int)(r / n), n);
+        int i_, j_, kz;
+        split3(q, n, nz, i_, j_, kz);
+        const int mj = freq(j_, n), mi = freq(i_, n);
         const int mc = c == 0 ? mi : (c == 1 ? mj : kz);
         const double kx = kf * mi, ky = kf * mj, kzz = kf * kz;
         const double k2 = kx * kx + ky * ky + kzz * kzz;
@@ -89,9 +89,8 @@ k_ic_place(const double *__restrict__ psi, int n, int c, double growth, double v
     const long long np = (long long)n * n * n;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np; p += stride) {
-        const int k = (int)(p % n);
-        const long long r = p / n;
-        const int j = (int)(r % n), i = (int)(r / n);
+        int i, j, k;
+        split3(p, n, n, i, j, k);
         const double q = (c == 0 ? i : (c == 1 ? j : k)) + 0.5;
         const double s = psi[p];
         double x = q + growth * s;
@@ -316,9 +315,8 @@ k_div64(const double *__restrict__ gb0, const double *__restrict__ gb1, const do
     const long long cnt = (long long)n * n * n;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
-        const int k = (int)(q % n);
-        const long long r = q / n;
-        const int j = (int)(r % n), i = (int)(r / n);
+        int i, j, k;
+        split3(q, n, n, i, j, k);
         const int ip = i + 1 == n ? 0 : i + 1, im = i == 0 ? n - 1 : i - 1;
         const int jp = j + 1 == n ? 0 : j + 1, jm = j == 0 ? n - 1 : j - 1;
         const int kp = k + 1 == n ? 0 : k + 1, km = k == 0 ? n - 1 : k - 1;
@@ -367,9 +365,9 @@ k_pk(const cufftDoubleComplex *__restrict__ spec, int n, int nbins, double vscal
     const long long total = (long long)n * n * nz;
     double v[2] = {0.0, 0.0};
     for (long long q = threadIdx.x; q < total; q += blockDim.x) {
-        const int kz = (int)(q % nz);
-        const long long r = q / nz;
-        const int mj = freq((int)(r % n), n), mi = freq((int)(r / n), n);
+        int i_, j_, kz;
+        split3(q, n, nz, i_, j_, kz);
+        const int mj = freq(j_, n), mi = freq(i_, n);
         if (pk_bin(mi, mj, kz, half, nbins) != b) continue;
         const double w = (kz > 0 && kz < half) ? 2.0 : 1.0;
         const cufftDoubleComplex c = spec[q];
@@ -391,9 +389,9 @@ k_pk_adj(cufftDoubleComplex *__restrict__ spec, int n, int nbins, const double *
     const long long total = (long long)n * n * nz;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += stride) {
-        const int kz = (int)(q % nz);
-        const long long r = q / nz;
-        const int mj = freq((int)(r % n), n), mi = freq((int)(r / n), n);
+        int i_, j_, kz;
+        split3(q, n, nz, i_, j_, kz);
+        const int mj = freq(j_, n), mi = freq(i_, n);
         const int b = pk_bin(mi, mj, kz, half, nbins);
         const double f = b >= 0 ? coef[b] : 0.0;
         cufftDoubleComplex c = spec[q];

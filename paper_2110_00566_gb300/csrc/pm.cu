@@ -114,9 +114,8 @@ k_green(cufftComplex *spec, int n, const float *__restrict__ t, float scale)
     const long long total = (long long)n * n * nz;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += stride) {
-        const int kz = (int)(q % nz);
-        const long long r = q / nz;
-        const int j = (int)(r % n), i = (int)(r / n);
+        int i, j, kz;
+        split3(q, n, nz, i, j, kz);
         cufftComplex v = spec[q];
         const float f = q == 0 ? 0.f : -scale / ((t[i] + t[j]) + t[kz]);
         v.x *= f;
@@ -159,9 +158,8 @@ k_poisson_resid(const double *__restrict__ u, const double *__restrict__ rhs, co
     const long long cnt = (long long)n * n * n;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
-        const int k = (int)(q % n);
-        const long long r = q / n;
-        const int j = (int)(r % n), i = (int)(r / n);
+        int i, j, k;
+        split3(q, n, n, i, j, k);
         const long long pl = (long long)n * n;
         const long long qip = i + 1 == n ? q - (n - 1) * pl : q + pl, qim = i == 0 ? q + (n - 1) * pl : q - pl;
         const long long qjp = j + 1 == n ? q - (long long)(n - 1) * n : q + n,
@@ -208,9 +206,11 @@ k_pot(const double *__restrict__ phin, const double *__restrict__ phi, double cp
         out[q] = pot(phin, phi, cphi, q);
 }
 
-// -grad Phi by 3-point differences on the mesh, g_c = -(Phi(+e_c) -
-// Phi(-e_c)) / 2 (the arithmetic of the per-corner force, so that the
-// interpolated force is bit-identical to evaluating it at the corners)
+// twice -grad Phi by 3-point differences on the mesh, 2 g_c = Phi(-e_c) -
+// Phi(+e_c): the per-corner force's -(Phi(+e_c) - Phi(-e_c)) / 2 without the
+// halving, which the kick applies to its factor instead (a power of two
+// commutes with every rounding, so the interpolated force is bit-identical
+// to evaluating it at the corners)
 __global__ void __launch_bounds__(256)
 k_force_mesh(const double *__restrict__ P, double *__restrict__ gx, double *__restrict__ gy, double *__restrict__ gz,
              int n)
@@ -218,22 +218,22 @@ k_force_mesh(const double *__restrict__ P, double *__restrict__ gx, double *__re
     const long long cnt = (long long)n * n * n, pl = (long long)n * n;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
-        const int k = (int)(q % n);
-        const long long r = q / n;
-        const int j = (int)(r % n), i = (int)(r / n);
+        int i, j, k;
+        split3(q, n, n, i, j, k);
         const long long qip = i + 1 == n ? q - (n - 1) * pl : q + pl, qim = i == 0 ? q + (n - 1) * pl : q - pl;
         const long long qjp = j + 1 == n ? q - (long long)(n - 1) * n : q + n,
                         qjm = j == 0 ? q + (long long)(n - 1) * n : q - n;
         const long long qkp = k + 1 == n ? q - (n - 1) : q + 1, qkm = k == 0 ? q + (n - 1) : q - 1;
-        gx[q] = -__dsub_rn(__ldg(P + qip), __ldg(P + qim)) / 2.0;
-        gy[q] = -__dsub_rn(__ldg(P + qjp), __ldg(P + qjm)) / 2.0;
-        gz[q] = -__dsub_rn(__ldg(P + qkp), __ldg(P + qkm)) / 2.0;
+        gx[q] = __dsub_rn(__ldg(P + qim), __ldg(P + qip));
+        gy[q] = __dsub_rn(__ldg(P + qjm), __ldg(P + qjp));
+        gz[q] = __dsub_rn(__ldg(P + qkm), __ldg(P + qkp));
     }
 }
 
 // the force at each particle interpolated from the mesh force with the CIC
 // weights, then the leapfrog kick and drift (code units of Sec. 3.1.1):
-//   p = p fr + g ck,  x += p cd,  wrap into [0, ng).  Phi = PhiN + cphi phi
+//   p = p fr + g ck,  x += p cd,  wrap into [0, ng)  (g2 = 2 g from the
+// mesh, ck2 = ck / 2: g2 ck2 = g ck exactly).  Phi = PhiN + cphi phi
 // when phi is given (nDGP: cphi = 1/2, Eq. poisson_nDGP; Kmouflage: cphi =
 // beta c~, Eq. force_Kmo2, whose friction term gives fr = 1 - beta
 // (dphibar/da) da_kick; fr = 1 otherwise).  Rounded as written (no
@@ -241,7 +241,7 @@ k_force_mesh(const double *__restrict__ P, double *__restrict__ gx, double *__re
 // formed once per (a, b)
 __global__ void __launch_bounds__(256)
 k_kick_drift(float *__restrict__ pos, float *__restrict__ mom, long long np, int ng, const double *__restrict__ gx,
-             const double *__restrict__ gy, const double *__restrict__ gz, double fr, double ck, double cd)
+             const double *__restrict__ gy, const double *__restrict__ gz, double fr, double ck2, double cd)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np; p += stride) {
@@ -267,7 +267,7 @@ k_kick_drift(float *__restrict__ pos, float *__restrict__ mom, long long np, int
             }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const float pn = (float)__dadd_rn(__dmul_rn((double)mom[3 * p + d], fr), __dmul_rn(g[d], ck));
+            const float pn = (float)__dadd_rn(__dmul_rn((double)mom[3 * p + d], fr), __dmul_rn(g[d], ck2));
             mom[3 * p + d] = pn;
             float x = (float)__dadd_rn((double)pos[3 * p + d], __dmul_rn((double)pn, cd));
             if (x < 0.f) x = __fadd_rn(x, (float)ng);
@@ -580,7 +580,7 @@ int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats)
         }
         k_force_mesh<<<grid1(cells), 256, 0, ctx->stream>>>(P, w.g3, w.g3 + cells, w.g3 + 2 * cells, n);
         k_kick_drift<<<grid1(st->np), 256, 0, ctx->stream>>>(dpos, dmom, st->np, n, w.g3, w.g3 + cells,
-                                                             w.g3 + 2 * cells, fr, ck, cd);
+                                                             w.g3 + 2 * cells, fr, 0.5 * ck, cd);
         MG_CK(cudaGetLastError());
         stage_out(ctx, st->pos, dpos, pb);
         stage_out(ctx, st->mom, dmom, pb);
