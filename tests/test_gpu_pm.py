@@ -14,13 +14,17 @@ pytestmark = pytest.mark.gpu
 from test_gpu_parity import B, ctx  # noqa: E402,F401
 
 
-def test_newton_potential(B, ctx):
-    n = 24
-    delta = inputs.white_noise(n, 70)
+@pytest.mark.parametrize("n", [24, 96, 256])
+@pytest.mark.parametrize("shift", [0.0, 0.3])
+def test_newton_potential(B, ctx, n, shift):
+    # the FP32 transforms inside the FP64 refinement against the oracle's
+    # FP64 solution; a source with a nonzero mean (which the zero mode drops)
+    delta = inputs.white_noise(n, 70) + shift
     ref = oracle.newton_potential(delta, 0.5, 0.3)
     out = np.empty_like(delta)
     B.pm_newton_potential(ctx, n, 0.5, 0.3, delta, out)
     assert np.abs(out - ref).max() < 1e-12 * np.abs(ref).max()
+    assert np.linalg.norm(out - ref) < 1e-13 * np.linalg.norm(ref)
 
 
 def _load(ng, nps, seed, a):
