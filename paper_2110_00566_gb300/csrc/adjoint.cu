@@ -326,11 +326,16 @@ struct AdjWork {
     std::vector<void *> blocks;
     double *scal = nullptr;   // [0..2]: sums, [8..]: per level m
     RedBuf rb{};
+    // one captured cycle (V-cycle, residual pass, copy of its sums to the
+    // pinned scratch) for the sweep counts it was captured with
+    cudaGraphExec_t cycle = nullptr;
+    int cycle_key[3] = {-1, -1, -1};
 };
 
 static void adj_free(AdjWork *w)
 {
     if (!w) return;
+    if (w->cycle) cudaGraphExecDestroy(w->cycle);
     for (void *p : w->blocks) cudaFree(p);
     if (w->scal) cudaFree(w->scal);
     delete w;
@@ -482,13 +487,36 @@ int adjoint_dev(mg_ctx *ctx, int n, double a, double om, double Rc, const mg_opt
     loc.n_eps = 1;
     int cyc = 0;
     bool conv = ref <= o.atol || ref == 0.0;
-    while (!conv && cyc < o.max_cycles) {
+    // every sweep flips a level's buffer twice, so a cycle leaves the buffer
+    // state as it found it and one captured cycle replays every cycle
+    auto record = [&]() {
         adj_vcycle(ctx, *w, 0, o);
-        ++cyc;
         k_mean_into<<<g1(cnt), 256, 0, s>>>(A0.lam[A0.cur], cnt, dscr + 8, w->rb);
         k_adj_resid<<<g1(cnt), 256, 0, s>>>(A0, A0.lam[A0.cur], dscr + 8, A0.res, w->rb, dscr);
-        MG_CK(cudaMemcpyAsync(h3, dscr, sizeof h3, cudaMemcpyDeviceToHost, s));
+        MG_CK(cudaMemcpyAsync(ctx->hpin, dscr, sizeof h3, cudaMemcpyDeviceToHost, s));
+    };
+    const int key[3] = {o.pre, o.post, o.coarse_sweeps};
+    if (o.use_graph && (!w->cycle || std::memcmp(key, w->cycle_key, sizeof key) != 0)) {
+        if (w->cycle) {
+            MG_CK(cudaGraphExecDestroy(w->cycle));
+            w->cycle = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        MG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        record();
+        MG_CK(cudaStreamEndCapture(s, &g));
+        MG_CK(cudaGraphInstantiate(&w->cycle, g, 0));
+        MG_CK(cudaGraphDestroy(g));
+        std::memcpy(w->cycle_key, key, sizeof key);
+    }
+    while (!conv && cyc < o.max_cycles) {
+        if (o.use_graph)
+            MG_CK(cudaGraphLaunch(w->cycle, s));
+        else
+            record();
+        ++cyc;
         MG_CK(cudaStreamSynchronize(s));
+        std::memcpy(h3, ctx->hpin, sizeof h3);
         const double eps = std::sqrt(h3[0] / (double)cnt);
         if (loc.n_eps < 65) loc.eps[loc.n_eps++] = eps;
         if (!std::isfinite(eps)) {

@@ -1,7 +1,8 @@
 """GPU parity of the adjoint nDGP solve (mg_solve_adjoint): gradients of
 L = <g, phi> with respect to delta and R_c against the FP64 oracle's
-dense-Jacobian reference gradient (8^3 and 16^3), and against central
-differences of the GPU's own forward solve (32^3)."""
+dense-Jacobian reference gradient (8^3, 12^3 -- whose coarsest level is
+6^3 -- and 16^3), and against central differences of the GPU's own forward
+solve (32^3)."""
 import numpy as np
 import pytest
 
@@ -23,7 +24,7 @@ def adjoint_gpu(B, ctx, delta, phi, g, a, om, rc, **kw):
     return out, drc, st
 
 
-@pytest.mark.parametrize("n,amp,rc", [(8, 3.0, 1.0), (16, 1.0, 1.0), (16, 2.0, 5.0)])
+@pytest.mark.parametrize("n,amp,rc", [(8, 3.0, 1.0), (12, 2.0, 1.0), (16, 1.0, 1.0), (16, 2.0, 5.0)])
 def test_adjoint_matches_oracle_reference(B, ctx, n, amp, rc):
     a, om = 1.0, 0.3
     delta = amp * inputs.white_noise(n, 300 + n)
