@@ -142,23 +142,25 @@ __global__ void __launch_bounds__(256) k_adj_v(AdjLev L)
 }
 
 // colour-simultaneous red-black update of J^T lambda = rhs with m = <lambda>
-// held fixed: lambda = (S6 - h^2 (rhs + M^T lambda - m v)) / 6
+// held fixed: lambda = (S6 - h^2 (rhs + M^T lambda - m v)) / 6.  A thread
+// takes one cell of the colour (k = 2 m' + k0 in its row) and copies its
+// row neighbour of the other colour into out, so that no warp splits between
+// the two (n is even)
 __global__ void __launch_bounds__(256)
 k_adj_smooth(AdjLev L, const double *__restrict__ in, double *__restrict__ out, const double *__restrict__ mscal,
              int colour)
 {
-    const int n = L.n;
-    const long long cnt = (long long)n * n * n;
+    const int n = L.n, hn = n / 2;
+    const long long hc = (long long)n * n * hn;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const double m = *mscal, h2 = L.h * L.h;
     const double *K[6] = {L.K[0], L.K[1], L.K[2], L.K[3], L.K[4], L.K[5]};
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += stride) {
-        int i, j, k;
-        split3(q, n, n, i, j, k);
-        if (((i + j + k) & 1) != colour) {
-            out[q] = in[q];
-            continue;
-        }
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < hc; t += stride) {
+        int i, j, mm;
+        split3(t, n, hn, i, j, mm);
+        const int k0 = (colour + i + j) & 1, k = 2 * mm + k0;
+        const long long q = nidx(i, j, k, n), qo = nidx(i, j, 2 * mm + 1 - k0, n);
+        out[qo] = in[qo];
         const double S6 = in[nidx(wrap_p(i, n), j, k, n)] + in[nidx(wrap_m(i, n), j, k, n)] +
                           in[nidx(i, wrap_p(j, n), k, n)] + in[nidx(i, wrap_m(j, n), k, n)] +
                           in[nidx(i, j, wrap_p(k, n), n)] + in[nidx(i, j, wrap_m(k, n), n)];
@@ -384,7 +386,7 @@ static void adj_vcycle(mg_ctx *ctx, AdjWork &w, int l, const mg_opts &o)
     double *mslot = w.scal + 8 + l;
     auto sweep = [&]() {
         for (int c = 0; c < 2; ++c) {
-            k_adj_smooth<<<g1(cnt), 256, 0, s>>>(A, A.lam[A.cur], A.lam[1 - A.cur], mslot, c);
+            k_adj_smooth<<<g1(cnt / 2), 256, 0, s>>>(A, A.lam[A.cur], A.lam[1 - A.cur], mslot, c);
             A.cur ^= 1;
         }
     };
