@@ -133,6 +133,20 @@ def test_prolongation(B, ctx, prec, n):
     assert rel(out, ref) < TOL[prec]
 
 
+@pytest.mark.parametrize("n,scale", [(128, 1.0), (256, 1.0), (128, 1e-300), (128, 1e300)])
+def test_prolongation_staged(B, ctx, n, scale):
+    # fine levels of 128^3 and more take the block-staged FP64 prolongation:
+    # the fixed-point path, and at 1e-300 (exponents below its domain) the
+    # FP64 path; 1e300 stays in the fixed-point domain
+    uf = scale * inputs.white_noise(n, 43)
+    uc = scale * inputs.white_noise(n // 2, 44)
+    urc = scale * inputs.white_noise(n // 2, 45)
+    ref = oracle.prolong_add(uf, uc, urc)
+    out = uf.copy()
+    B.mg_op_prolong_add(ctx, 0, n, out, uc, urc)
+    assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("name", list(MODELS))
 @pytest.mark.parametrize("n", [4, 6])
 def test_coarsest(B, ctx, name, n):
