@@ -290,7 +290,8 @@ int mg_solve_kmouflage(mg_ctx *ctx, const mg_grid *g, const mg_kmo_params *p,
  * Linear-theory Kmouflage field (Eq. kmf_eqn_codeunit_lin): the gradient
  * term of the denominator and the T term dropped,
  *   Lap phi = 3 beta A Omega_m a^-1 (delta - <delta>) / [c~ (1 + gamma (phibar'/H0)^(2(n-1)))],
- * solved by FFT with the 7-point Green's function (the multigrid Laplacian);
+ * solved by FFT with the 7-point Green's function (the multigrid Laplacian;
+ * FP32 transforms inside an FP64 refinement, as pm_newton_potential);
  * the screening-off reference for mg_solve_kmouflage.  ng even >= 2.
  * Errors: MG_ERR_ARG, MG_ERR_CUDA, MG_ERR_OOM.
  */
@@ -343,8 +344,11 @@ int pm_cic_index(mg_ctx *ctx, int ng, const float *pos, long long np,
 
 /* Newtonian potential on the mesh (Sec. 3.1; Eq. GR_poisson_codeunit):
  * Lap Phi = (3/2) Omega_m a^-1 delta with the 7-point Laplacian, solved by
- * FFT (cuFFT, FP64) with the Green's function -1/sum_d 4 sin^2(pi k_d/ng);
- * the k = 0 mode is set to zero.  delta, phi_out: ng^3 FP64 (ng even). */
+ * FFT with the Green's function -1/sum_d 4 sin^2(pi k_d/ng); the k = 0 mode
+ * is set to zero (the mean of delta is ignored).  The transforms run in
+ * FP32 (cuFFT) inside an FP64 iterative refinement (two corrections from
+ * FP64 residuals of the 7-point system), which returns the FP64 solution to
+ * about 1e-15 relative.  delta, phi_out: ng^3 FP64 (ng even). */
 int pm_newton_potential(mg_ctx *ctx, int ng, double a, double omega_m,
                         const double *delta, double *phi_out);
 
@@ -381,7 +385,7 @@ typedef struct {
  * the drift sign of Eq. force_Kmo1): CIC density, FFT Poisson solve of
  * Lap Phi_N = (3/2) Omega_m a^-1 delta with the 7-point Green's function,
  * the nDGP field (model 1), 3-point gradient of Phi at the 8 CIC cells
- * interpolated to each particle, kick p += g da/(a E(a)) (da/2 if first),
+ * (formed once per mesh cell) interpolated to each particle, kick p += g da/(a E(a)) (da/2 if first),
  * drift x += p da/(a_m^3 E(a_m)) with a_m = a + da/2, wrap into [0, ng);
  * E = H/H0 (e_a, e_mid when set).
  * Updates pos, mom, a (+= da) and first (= 0).  stats: the nDGP solve.
