@@ -311,8 +311,7 @@ int pm_cic_deposit(mg_ctx *ctx, int ng, const float *pos, long long np,
                    double *delta_out);
 
 /*
- * pm_cic_deposit for callers that cannot allocate device memory: code
- * running while a CUDA graph is captured (allocation is illegal there),
+ * pm_cic_deposit for callers that cannot allocate device memory:
  * applications whose device memory all belongs to their own pool, and
  * pipelines that cannot afford the device synchronisation of cudaMalloc.
  * The paper has no counterpart; this is a deployment variant of the CIC
@@ -327,8 +326,7 @@ int pm_cic_deposit(mg_ctx *ctx, int ng, const float *pos, long long np,
  *    current device; work is queued on cuda_stream (a cudaStream_t, NULL =
  *    legacy default stream) and the call returns without synchronising.
  *  - The first call on a device (the current one) looks up the array's
- *    device address with cudaGetSymbolAddress; make that first call before
- *    any stream capture.
+ *    device address with cudaGetSymbolAddress.
  *  - Every call shares the one array, which keeps the last call's contents
  *    (each call clears what must start at zero): calls whose work overlaps
  *    on the GPU (other streams, other threads) race and corrupt each other.

@@ -601,10 +601,9 @@ int pm_step(mg_ctx *ctx, pm_state *st, const mg_opts *opts, mg_stats *stats)
 //
 // pm_cic_deposit keeps its fixed-point accumulator and reduction partials in
 // memory it allocates on first use.  Some callers cannot let a library call
-// cudaMalloc: code that runs while a CUDA graph is being captured (an
-// allocation there is illegal), applications that hand all device memory to
-// their own pool up front, and real-time pipelines in which cudaMalloc's
-// implicit device synchronisation is not acceptable.  This variant runs the
+// cudaMalloc: applications that hand all device memory to their own pool up
+// front, and real-time pipelines in which cudaMalloc's implicit device
+// synchronisation is not acceptable.  This variant runs the
 // same kernels with all of its scratch in one file-scope device array whose
 // size is fixed when the library is loaded: the accumulator for meshes up
 // to NOALLOC_MAX_NG^3 cells, the reduction partials, the mean and the

@@ -1,6 +1,6 @@
 """The allocation-free CIC deposit (pm_cic_deposit_noalloc) for callers that
-cannot let a library allocate device memory (graph capture, caller-owned
-memory pools, pipelines that cannot take cudaMalloc's synchronisation).
+cannot let a library allocate device memory (caller-owned memory pools,
+pipelines that cannot take cudaMalloc's synchronisation).
 
 Called through the C-ABI on device arrays, several times in a row with
 different particle loads and mesh sizes up to the scratch array's limit of
