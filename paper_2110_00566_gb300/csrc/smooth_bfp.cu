@@ -126,7 +126,9 @@ k_smooth_bfp(const double *__restrict__ Uc, const double *__restrict__ Uo, doubl
 // the block-fixed-point half-sweep for levels of 128^3 and more with
 // half % 32 == 0 and n % 16 == 0; false otherwise (coarser levels have too
 // few tiles to fill the GPU with marching blocks); planes per block: 16,
-// fewer where that leaves under ~4 blocks per SM
+// halved (down to 2) while that leaves under about 4 waves of 4 blocks per
+// SM (measured at 256^3: 4 planes 0.184 ms, 16 planes 0.193 ms, the last
+// wave of 1024 blocks two-thirds full)
 bool launch_smooth_bfp(const LevArrays<double> &L, const LevK<double> &K, const OpK<double> *op, int colour, int nb,
                        cudaStream_t st)
 {
@@ -134,7 +136,7 @@ bool launch_smooth_bfp(const LevArrays<double> &L, const LevK<double> &K, const 
         return false;
     const long long tiles = (long long)(L.half / bfp::TM) * (L.n / SM_TJ);
     int zc = 16;
-    while (zc > 2 && tiles * ((L.n + zc - 1) / zc) < 600) zc /= 2;
+    while (zc > 2 && tiles * ((L.n + zc - 1) / zc) < 2400) zc /= 2;
     const dim3 b(bfp::TM, bfp::THREADS / bfp::TM, 1);
     const dim3 g(L.half / bfp::TM, L.n / SM_TJ, (L.n + zc - 1) / zc);
 #define MG_SBF(HASF, MODEL)                                                                                    \
