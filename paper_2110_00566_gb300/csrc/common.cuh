@@ -487,6 +487,52 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], const RedBuf &rb, doub
     return true;
 }
 
+// grid_sum for NV FP64 sums and one integer count per thread (a flag count:
+// reduced on the integer pipe, so that it costs no FP64 add per thread);
+// tot[0 .. NV-1] are the sums, tot[NV] the count (exact as a double).  The
+// sums come out bit-identical to grid_sum's: each value's reduction tree
+// does not depend on the others.  Every thread of the block must call it.
+template <int NV>
+__device__ __forceinline__ bool grid_sum_cnt(double (&v)[NV], int cnt, const RedBuf &rb, double (&tot)[NV + 1])
+{
+    __shared__ double sh[32 * (NV + 1)];
+    __shared__ bool last;
+    __shared__ unsigned int scnt;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    if (tid == 0) scnt = 0u;
+    __syncthreads();
+    const unsigned wc = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+    if ((tid & 31) == 0) atomicAdd(&scnt, wc);
+    block_sum<NV>(v, sh);   // (its barriers also order the count's atomics before thread 0 reads it)
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) rb.partials[(size_t)bid * (NV + 1) + q] = v[q];
+        rb.partials[(size_t)bid * (NV + 1) + NV] = (double)scnt;
+        __threadfence();
+        const unsigned t = atomicAdd(rb.counter, 1u);
+        last = (t == nb - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[NV + 1];
+#pragma unroll
+    for (int q = 0; q <= NV; ++q) acc[q] = 0.0;
+    const unsigned per = (nb + nthreads - 1) / nthreads;
+    const unsigned b0 = tid * per, b1 = min(nb, b0 + per);
+    for (unsigned b = b0; b < b1; ++b)
+#pragma unroll
+        for (int q = 0; q <= NV; ++q) acc[q] += __ldcg(rb.partials + (size_t)b * (NV + 1) + q);
+    block_sum<NV + 1>(acc, sh);
+#pragma unroll
+    for (int q = 0; q <= NV; ++q) tot[q] = acc[q];
+    if (tid == 0) *rb.counter = 0u;
+    return true;
+}
+
 // The same deterministic reduction over `nb` work tiles of one problem when
 // a persistent block processes tiles of several problems: tile `bid`
 // stores its block sums, and the block that stores the last one sums all

@@ -288,11 +288,10 @@ template <typename T>
 void launch_resid_norm(const LevArrays<T> &L, const OpK<T> *op, const RedBuf &rb, cudaStream_t st,
                        float *const *D, bool zero_u)
 {
-    // (a zero field on an eligible level runs the same kernel as any other
-    // field, so that its norms come out bit-identical to a warm start from
-    // an explicit zero field)
+    // (a zero field takes the zero-field variants, whose norms come out
+    // bit-identical to those of the same pass over an explicit zero field)
     if constexpr (sizeof(T) == 8) {
-        if (launch_resid_norm_bfp(L, op, rb, st, D)) return;
+        if (launch_resid_norm_bfp(L, op, rb, st, D, zero_u)) return;
     }
     const dim3 b = block_mj(L.half);
     dim3 g = grid_mj(L.half, L.n, b, 1);

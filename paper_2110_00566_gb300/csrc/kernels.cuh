@@ -55,7 +55,7 @@ bool launch_smooth_bfp(const LevArrays<double> &L, const LevK<double> &K, const 
 bool launch_resid_restrict_bfp(const LevArrays<double> &Lf, LevArrays<double> &Lc, const OpK<double> *op,
                                const RedBuf &rb, cudaStream_t st);
 bool launch_resid_norm_bfp(const LevArrays<double> &L, const OpK<double> *op, const RedBuf &rb, cudaStream_t st,
-                           float *const *D);
+                           float *const *D, bool zero_u);
 // the coarse level's FAS source (Eq. general_pde_numerical_coarse) on the
 // block-staged kernel (resid_bfp.cu); false when the coarse level is not
 // eligible

@@ -38,8 +38,12 @@ constexpr int RR_TJ = 8;   // tile rows: a warp covers 16 columns of two rows
 
 // MODE: above; HASF: the level has a FAS source f (every level but the
 // finest; in MODE 2 f is R d, read and overwritten through FW0, FW1, and the
-// shift is -dc of the fine level, scf); MODEL: 0 nDGP, 1 Kmouflage
-template <int MODE, bool HASF, int MODEL>
+// shift is -dc of the fine level, scf); MODEL: 0 nDGP, 1 Kmouflage; ZERO
+// (MODE 0): u is known to vanish everywhere (a solve from phi = 0), so
+// nothing is staged: the stencil's sums are the zeros a staged zero field
+// gives at its scale (that of 1.0), and every result is bit-identical to
+// the pass over an explicit zero field
+template <int MODE, bool HASF, int MODEL, bool ZERO = false>
 __global__ void __launch_bounds__(bfp::THREADS, 3)
 k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const double *__restrict__ S0,
             const double *__restrict__ S1, const double *__restrict__ F0, const double *__restrict__ F1, LevScal *sc,
@@ -65,14 +69,16 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
     }
     // ring colour slots: 0 = the colour-0 array, 1 = the colour-1 array
     bfp::Stager<RR_TJ> g(t, U0, U1, n, half, m0, j0, tid);
-    g.fill(i0);
+    static_assert(!ZERO || MODE == 0, "the zero-field variant is a norm pass");
+    if (!ZERO) g.fill(i0);   // (its barriers also publish thread 0's constants above)
+    else __syncthreads();
     const double c_old = s_c[0], cshift = s_c[1];
     const NtK nk = s_nk;
     const OpK<double> &op = *opp;
     const bfp::KmoK kk = MODEL == 1 ? bfp::make_kmok(op, L) : bfp::KmoK{0.0, 0.0, 0};
     const int j = j0 + jt, m = m0 + mt;
     const int jj = jt + 1, mm = mt + 1;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};   // sum N, sum d, sum d^2, clamps
+    double acc[3] = {0.0, 0.0, 0.0};        // sum N, sum d, sum d^2
     int nclamp = 0;                         // (counted in an integer: no FP64 add per cell)
     double su = 0.0, sd = 0.0;              // this thread's children of the coarse cell
     // the pass's constant shift h^2 cshift folded into the fixed-point
@@ -100,7 +106,7 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
         const long long rowi = (long long)i * g.pstride + rowo;
         const double sv[2] = {s_nx[0], s_nx[1]}, fv[2] = {f_nx[0], f_nx[1]};
         if (more) {
-            g.prefetch(i + 2);
+            if (!ZERO) g.prefetch(i + 2);
             s_nx[0] = __ldg(S0 + rowi + g.pstride);
             s_nx[1] = __ldg(S1 + rowi + g.pstride);
             if (HASF) {
@@ -121,14 +127,16 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
             double N, d;
             int cl = 0;
             if (fx) {
-                const bfp::Sums r = bfp::stencil<RR_TJ>(t.v[g.sm], t.v[g.s0], t.v[g.sp], c, jj, mm, p);
-                const long long U = bfp::at<RR_TJ>(t.v[g.s0], c, jj, mm);
+                const bfp::Sums r = ZERO ? bfp::Sums{0, 0, 0, 0, 0, 0}
+                                         : bfp::stencil<RR_TJ>(t.v[g.sm], t.v[g.s0], t.v[g.sp], c, jj, mm, p);
+                const long long U = ZERO ? 0 : bfp::at<RR_TJ>(t.v[g.s0], c, jj, mm);
                 Usum += U;
                 const long long lap6 = (r.X + r.Y + r.Z) - ((U << 2) + (U << 1));   // |.| < 12 * 2^59
                 if (MODEL == 0) {
                     N = dgp64_N_any(op, dk, nk, bfp::quad(r, g.ef), s, cl);
                 } else {
-                    const bfp::Diffs dd = bfp::diffs<RR_TJ>(t.v[g.sm], t.v[g.s0], t.v[g.sp], c, jj, mm, p);
+                    const bfp::Diffs dd = ZERO ? bfp::Diffs{0, 0, 0}
+                                               : bfp::diffs<RR_TJ>(t.v[g.sm], t.v[g.s0], t.v[g.sp], c, jj, mm, p);
                     N = bfp::kmo64_N(op, kk, r, dd, s, g.ef);
                 }
                 if (FOLD)
@@ -189,15 +197,20 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
             su = 0.0;
         }
         if (!more) break;
-        g.advance(step, i);
+        if (!ZERO) g.advance(step, i);
         kv = bfp::fold(kc, g.ef, kok);
     }
-    acc[3] = (double)nclamp;
-    double tot[4];
-    if (grid_sum<4>(acc, rb, tot) && tid == 0) {
+    // the restriction and coarse-source passes reduce only sum N (and the
+    // clamp count, on the integer pipe)
+    constexpr int NR = (RR || CS) ? 1 : 3;
+    double red[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) red[q] = acc[q];
+    double tot[NR + 1];
+    if (grid_sum_cnt<NR>(red, nclamp, rb, tot) && tid == 0) {
         const double cnt = (double)n * n * n;
         const double c_new = tot[0] / cnt;
-        if (CS) {
+        if constexpr (CS) {
             set_c_fshift(sc, c_new, c_new);
             sc->dc = 0.0;
         } else {
@@ -206,11 +219,13 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
             sc->dc = dc;
             // (the restriction pass sums neither d nor d^2: its residual norm
             // is not used, and the norm pass gives it where it is)
-            sc->eps2 = RR ? __longlong_as_double(0x7FF8000000000000LL)
-                          : (tot[2] + 2.0 * dc * tot[1] + cnt * dc * dc) / cnt;
+            if constexpr (RR)
+                sc->eps2 = __longlong_as_double(0x7FF8000000000000LL);
+            else
+                sc->eps2 = (tot[2] + 2.0 * dc * tot[1] + cnt * dc * dc) / cnt;
         }
         sc->sumN = tot[0];
-        sc->clamps = tot[3];
+        sc->clamps = tot[NR];
     }
 }
 
@@ -255,24 +270,27 @@ bool launch_resid_restrict_bfp(const LevArrays<double> &Lf, LevArrays<double> &L
 }
 
 bool launch_resid_norm_bfp(const LevArrays<double> &L, const OpK<double> *op, const RedBuf &rb, cudaStream_t st,
-                           float *const *D)
+                           float *const *D, bool zero_u)
 {
     if (!bfp_eligible(L)) return false;
     const int zc = bfp_planes(L, rb.cap);
     const dim3 b(bfp::THREADS, 1, 1);
     const dim3 g(L.half / bfp::TM, L.n / RR_TJ, (L.n + zc - 1) / zc);
     if ((long long)g.x * g.y * g.z > rb.cap) return false;
-#define MG_RNB(HASF, MODEL)                                                                                   \
-    k_resid_bfp<0, HASF, MODEL><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb,           \
+#define MG_RNB(HASF, MODEL, ZERO)                                                                             \
+    k_resid_bfp<0, HASF, MODEL, ZERO><<<g, b, 0, st>>>(L.U(0), L.U(1), L.s[0], L.s[1], L.f[0], L.f[1], L.sc, rb,           \
                                               make_levk<double>(L.n, L.h), op, nullptr, nullptr, nullptr, nullptr, \
                                               nullptr, nullptr, D ? D[0] : nullptr, D ? D[1] : nullptr, nullptr,  \
                                               nullptr, nullptr, make_dgpk64(L.h), zc)
-    if (L.model == 0) {
-        if (L.f[0]) MG_RNB(true, 0);
-        else MG_RNB(false, 0);
+    if (zero_u && !L.f[0]) {
+        if (L.model == 0) MG_RNB(false, 0, true);
+        else MG_RNB(false, 1, true);
+    } else if (L.model == 0) {
+        if (L.f[0]) MG_RNB(true, 0, false);
+        else MG_RNB(false, 0, false);
     } else {
-        if (L.f[0]) MG_RNB(true, 1);
-        else MG_RNB(false, 1);
+        if (L.f[0]) MG_RNB(true, 1, false);
+        else MG_RNB(false, 1, false);
     }
 #undef MG_RNB
     return true;
