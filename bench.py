@@ -432,13 +432,20 @@ def main():
         clocks = Clocks(local)
         clocks.start()
         t0 = time.perf_counter()
-        upd = 0
+        upd, solve_ms = 0, 0.0
         for _ in range(a.steps):
             _, st = B.mg_solve_dgp(ctx, [insth], r["o"])
             upd += st[0].cell_updates
-        dt, upd = reduce_max_sum(time.perf_counter() - t0, upd)
+            solve_ms += st[0].ms
+        wall = time.perf_counter() - t0
+        dt, upd = reduce_max_sum(wall, upd)
+        # the library's own device time of each solve (events around the
+        # solve on its stream, copies excluded) beside the wall time per call
         return {"value": upd / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * ng ** 3,
-                "d2h_bytes_per_step": 8 * ng ** 3, "clocks": clocks.stop()}
+                "d2h_bytes_per_step": 8 * ng ** 3, "ms_per_step": 1e3 * wall / a.steps,
+                "solve_ms_per_step": solve_ms / a.steps,
+                "host_copy_gbs": 2 * 8 * ng ** 3 / max(1e-9, wall / a.steps - 1e-3 * solve_ms / a.steps) / 1e9,
+                "clocks": clocks.stop()}
 
     # DRAM bytes (read + write) per launch of the dominant kernels from ncu,
     # with the mesh they were measured on (profiles/k_smooth_bfp_fp64_ndgp_256.md
