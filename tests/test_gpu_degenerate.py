@@ -15,7 +15,9 @@ of 128^3 and more that run the block-staged FP64 kernels:
   the oracle's solution;
 * the FP64 solve, which measures its residual norm only on the cycles its
   rate prediction selects, stops at the same cycle as the oracle, which
-  measures every cycle (no cycle wasted, none skipped)."""
+  measures every cycle (no cycle wasted, none skipped);
+* cells far outside the physical range, where the square-root argument of
+  N is negative: clamped and counted as the oracle counts them."""
 import numpy as np
 import pytest
 
@@ -147,3 +149,25 @@ def test_full_128_kmouflage_solve_against_the_oracle(B, ctx, field128):
     code, _ = B.mg_solve_kmouflage(ctx, n, box, a, om, 2, 1.0, 0.2, lam, -1e-3, np.exp(-0.02), delta, phi,
                                    B.opts(rtol=1e-10, max_cycles=60))
     assert code == 0 and l2(phi, ref) < 1e-8, l2(phi, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [32, 128])
+def test_sqrt_clamps_are_counted(B, ctx, n, prec):
+    """Twelve seeded cells at delta = -100, far beyond the physical range
+    (delta >= -1), where alpha^2 + 8 Sigma / 3 < 0: N takes the printed
+    form's limit -(3/4) alpha there and the cell is counted (the clamp
+    reading of the square root of a negative argument).  The count of the
+    solve's final residual pass equals the oracle's, and phi matches the
+    oracle's solution (per-thread kernels at 32^3, block-staged ones at
+    128^3, whose passes reduce the count on the integer pipe)."""
+    d = 2.0 * inputs.white_noise(n, 77)
+    rng = np.random.default_rng(5)
+    for i, j, k in rng.integers(0, n, size=(12, 3)):
+        d[i, j, k] = -100.0
+    ref, rst = oracle.dgp_solve(d, 1.0, 0.3, 1.0, oracle.Opts(rtol=1e-11, max_cycles=60))
+    assert rst.sqrt_clamps == 12
+    phi, code, st = solve(B, ctx, d, prec=prec, rtol=1e-9)
+    assert code == 0, st.eps_list()
+    assert st.sqrt_clamps == rst.sqrt_clamps
+    assert l2(phi, ref) < (1e-7 if prec == 0 else 1e-6), l2(phi, ref)
