@@ -163,11 +163,6 @@ __device__ __forceinline__ float4 quad_from_slots(const OpK<float> &op, const Le
     }
 }
 
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 // sequence plane q of a block's share [u0, u1) of (j-tile, plane) units:
 // the share is walked as runs of consecutive planes of one j-tile, and run
 // (jt, ia .. ib-1) contributes planes ia-1 .. ib (ib - ia + 2 of them)
