@@ -120,8 +120,9 @@ int mg_probe_fp64_math(mg_ctx *ctx, int fn, const double *x, double *y, long lon
 
 /* ---- problem description (Sec. 3.1.1, 3.2.3, 3.2.4) ------------------- */
 typedef struct {
-    int ng;            /* cells per side: 2^k or 3 * 2^k, ng >= 8 (levels halve
-                          to a 4^3 or 6^3 coarsest mesh, Sec. 3.2.1)          */
+    int ng;            /* cells per side: 2^k or 3 * 2^k, 8 <= ng <= 1536
+                          (levels halve to a 4^3 or 6^3 coarsest mesh, Sec.
+                          3.2.1; above 1536 MG_ERR_ARG)                       */
     double box_mpch;   /* box side L in Mpc/h                                  */
     double a;          /* scale factor                                         */
     double omega_m;    /* present-day matter density parameter                 */

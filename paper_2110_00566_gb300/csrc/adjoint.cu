@@ -557,7 +557,7 @@ extern "C" int mg_solve_adjoint(mg_ctx *ctx, const mg_grid *g, const mg_dgp_para
 {
     if (!ctx) return MG_ERR_ARG;
     if (!g || !p || !phi || !delta || !dL_dphi || !dL_ddelta_out) return set_err(ctx, MG_ERR_ARG, "null argument");
-    if (!valid_ng(g->ng)) return set_err(ctx, MG_ERR_ARG, "ng = %d is not 2^k or 3*2^k >= 8", g->ng);
+    if (!valid_ng(g->ng)) return set_err(ctx, MG_ERR_ARG, "ng = %d is not 2^k or 3*2^k in [8, 1536]", g->ng);
     if (!(g->a > 0) || !(g->omega_m > 0) || !(p->rc_h0 > 0)) return set_err(ctx, MG_ERR_ARG, "bad parameters");
     mg_opts o;
     if (opts)

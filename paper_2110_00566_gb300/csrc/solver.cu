@@ -88,9 +88,13 @@ size_t level_count(int n)
     return c;
 }
 
+// 2^k or 3 * 2^k cells per side, at least 8 and at most 1536: the level
+// pyramid's colour arrays stay below 2^31 elements and the mesh below 2^32
+// cells, the index ranges the kernels are written for (2048^3 would not fit
+// one GPU's memory in any case: its FP64 finest level alone is ~340 GB)
 bool valid_ng(int n)
 {
-    if (n < 8) return false;
+    if (n < 8 || (long long)n * n * n >= (1LL << 32)) return false;
     int m = n;
     while (m % 2 == 0) m /= 2;
     return m == 1 || m == 3;
@@ -913,7 +917,7 @@ int mg_solve_dgp(mg_ctx *ctx, int count, const mg_instance *inst, const mg_opts 
     for (int q = 0; q < count; ++q) {
         const mg_instance &I = inst[q];
         if (!I.delta || !I.phi) return set_err(ctx, MG_ERR_ARG, "instance %d: null delta/phi", q);
-        if (!valid_ng(I.g.ng)) return set_err(ctx, MG_ERR_ARG, "instance %d: ng = %d is not 2^k or 3*2^k >= 8", q, I.g.ng);
+        if (!valid_ng(I.g.ng)) return set_err(ctx, MG_ERR_ARG, "instance %d: ng = %d is not 2^k or 3*2^k in [8, 1536]", q, I.g.ng);
         if (!(I.g.a > 0) || !(I.g.omega_m > 0) || !(I.p.rc_h0 > 0))
             return set_err(ctx, MG_ERR_ARG, "instance %d: a, omega_m and rc_h0 must be > 0", q);
     }
@@ -959,7 +963,7 @@ int mg_solve_kmouflage(mg_ctx *ctx, const mg_grid *g, const mg_kmo_params *p, co
 {
     if (!ctx) return MG_ERR_ARG;
     if (!g || !p || !delta || !phi) return set_err(ctx, MG_ERR_ARG, "null argument");
-    if (!valid_ng(g->ng)) return set_err(ctx, MG_ERR_ARG, "ng = %d is not 2^k or 3*2^k >= 8", g->ng);
+    if (!valid_ng(g->ng)) return set_err(ctx, MG_ERR_ARG, "ng = %d is not 2^k or 3*2^k in [8, 1536]", g->ng);
     if (p->n < 2 || p->k0 < 0 || !(g->a > 0) || !(g->box_mpch > 0) || !(p->lambda > 0))
         return set_err(ctx, MG_ERR_ARG, "bad Kmouflage parameters");
     mg_opts o;

@@ -29,6 +29,10 @@ def test_solver_argument_and_input_errors(B, ctx):
                                             phi=np.zeros((10,) * 3))]) == B.MG_ERR_ARG
     assert _code(B.mg_solve_dgp, ctx, [dict(ng=n, a=1.0, omega_m=0.3, rc_h0=0.0, delta=delta, phi=phi)]) == \
         B.MG_ERR_ARG
+    # a mesh above the supported 1536^3, rejected on the host before any
+    # array is read (the arrays passed are the small ones)
+    assert _code(B.mg_solve_dgp, ctx, [dict(ng=2048, a=1.0, omega_m=0.3, rc_h0=1.0, delta=delta, phi=phi)]) == \
+        B.MG_ERR_ARG
     # an unknown cycle type; odd pre + post with several device instances is
     # not the batched form: the instances are solved one after another
     two = [dict(ng=n, a=1.0, omega_m=0.3, rc_h0=1.0, delta=torch.from_numpy(delta).cuda(),
