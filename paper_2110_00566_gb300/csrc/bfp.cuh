@@ -87,8 +87,11 @@ __device__ __forceinline__ long long at(const long long *slot, int c, int r, int
 // of the block stages one colour: thread tid holds elements
 // e = tid % HT + q HT (q < PC) of colour tid / HT's plane, so that its global
 // array and shared-memory row are fixed and only the last element can fall
-// outside the plane.
-template <int TJ, int TMc = TM, int S = 6>
+// outside the plane.  NEAR: stage each value by two 32-bit funnel shifts
+// where it lies within 32 binades of the scale (the usual case; identical
+// result), the general 64-bit shift otherwise (fewer instructions per
+// staged value, more live registers: the smoother takes it).
+template <int TJ, int TMc = TM, int S = 6, bool NEAR = false>
 struct Stager {
     static constexpr int PLANE = Tile<TJ, TMc>::PLANE, LOAD = Tile<TJ, TMc>::LOAD;
     static constexpr int Wc = Tile<TJ, TMc>::Wc;
@@ -143,12 +146,18 @@ struct Stager {
         e = __reduce_max_sync(0xffffffffu, e);
         if ((tid & 31) == 0) atomicMax(&t.emax[slot], e);
     }
+    __device__ static long long cv(double v, int e)
+    {
+        if (!NEAR) return fx_in<S>(v, e);
+        const unsigned sh = (unsigned)(e - (__double2hiint(v) & 0x7FF00000)) >> 20;
+        return sh < 32 ? fx_in_near<S>(v, e) : fx_in<S>(v, e);
+    }
     __device__ void store(int s)
     {
         long long *d = t.v[s] + sb;
 #pragma unroll
         for (int q = 0; q < PC; ++q)
-            if (in(q)) d[q * HT] = fx_in<S>(x[q], ef);
+            if (in(q)) d[q * HT] = cv(x[q], ef);
     }
     __device__ void shift_down(int s, unsigned d)
     {
