@@ -451,7 +451,7 @@ def main():
     # with the mesh they were measured on (profiles/k_smooth_bfp_fp64_ndgp_256.md
     # and profiles/k_smooth4_fp32corr_ndgp_512.md, both at 512^3), scaled by
     # the cell count to this mesh
-    TRAFFIC = {"fp64": (1675.9e6 + 516.1e6, 512), "mixed": (1670.8e6 + 255.4e6, 512)}
+    TRAFFIC = {"fp64": (1676.4e6 + 515.9e6, 512), "mixed": (1670.8e6 + 255.4e6, 512)}
 
     def roofline(r, precision, fp64_tf):
         """Roofline of the finest half-sweep, anchored to the HBM peak (the
