@@ -68,7 +68,7 @@ k_resid_bfp(const double *__restrict__ U0, const double *__restrict__ U1, const 
         s_nk = make_ntk(*opp, dk);
     }
     // ring colour slots: 0 = the colour-0 array, 1 = the colour-1 array
-    bfp::Stager<RR_TJ> g(t, U0, U1, n, half, m0, j0, tid);
+    bfp::Stager<RR_TJ, bfp::TM, 6, !HASF> g(t, U0, U1, n, half, m0, j0, tid);
     static_assert(!ZERO || MODE == 0, "the zero-field variant is a norm pass");
     if (!ZERO) g.fill(i0);   // (its barriers also publish thread 0's constants above)
     else __syncthreads();
