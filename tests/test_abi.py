@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads, and exports every function
-that include/mgglam.h declares (no GPU needed: nothing is called)."""
+that include/mgglam.h declares (no GPU needed: nothing is called); without
+it the binding raises instead of falling back to anything."""
 import os
 import re
 
@@ -52,3 +53,15 @@ def test_product_package_does_not_import_the_oracle():
 def test_library_is_built_for_sm_103a(lib):
     from paper_2110_00566_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without the built library every entry point raises: there is no CPU
+    fallback for the product path to route through."""
+    from paper_2110_00566_gb300 import binding as B
+    monkeypatch.setattr(B, "_lib", None)
+    monkeypatch.setattr(B, "LIB_PATH", os.path.join(os.path.dirname(B.LIB_PATH), "no_such_libmgglam.so"))
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        B.lib()
+    with pytest.raises(ImportError):
+        B.Context(0)
